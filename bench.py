@@ -1,0 +1,326 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the fused phase-field LB step on GB300.
+
+Workload: 2-D Rayleigh-Taylor instability on a 16384 x 16384 grid (Atwood
+0.5, Re = 3000, d = 16384, 32 seeded random interface modes), conservative
+Allen-Cahn phase field, consistent-flux hydrodynamics, FP32, periodic in x
+with no-flux / no-slip walls in y (Sec. 4.4 of the paper, at the throughput
+size).  One benchmark step = one time step of the whole grid = one launch of
+the fused kernel; the metric is million lattice updates per second (phase +
+flow per node), summed over GPUs.
+
+`python bench.py [--gpus N --steps K --warmup W]` prints one JSON line.
+Under torchrun each rank runs its own full-size replica (weak scaling: the
+path shards into independent replicas, there is no data-path collective).
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "fused-step MLUPS (phase+flow) and % HBM roofline; adjoint/forward time ratio"
+UNIT = "MLUPS"
+FALLBACK_HBM_GBS = 6800.0
+VALUES_PER_LU = 46  # 18 populations + 5 history values, read and written
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="pflbm", choices=["pflbm", "reference"])
+    ap.add_argument("--n", type=int, default=16384, help="grid side")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload_name(n):
+    return f"rti_multimode_{n}x{n}_atwood0.5_re3000_ac"
+
+
+# ---------------------------------------------------------------------------
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            flat = {}
+
+            def walk(o, pre=""):
+                if isinstance(o, dict):
+                    for k, v in o.items():
+                        walk(v, f"{pre}{k}.")
+                else:
+                    flat[pre[:-1]] = o
+            walk(d)
+            for k, v in flat.items():
+                if "hbm" in k.lower() and isinstance(v, (int, float)) and "sustain" not in k.lower():
+                    return float(v), "of measured"
+            for k, v in flat.items():
+                if "hbm" in k.lower() and isinstance(v, (int, float)):
+                    return float(v), "of measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "of fallback"
+
+
+def profiled_traffic(esize):
+    """DRAM bytes per lattice update of the step kernel, from the committed
+    ncu summary (profiles/*.txt line 'dram_bytes_per_lu_fp32: X')."""
+    key = "dram_bytes_per_lu_fp32" if esize == 4 else "dram_bytes_per_lu_fp64"
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.txt"))):
+        for line in open(f):
+            m = re.match(rf"\s*{key}\s*:\s*([0-9.eE+-]+)", line)
+            if m:
+                return float(m.group(1)), os.path.basename(f)
+    return None, None
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"pflbm_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(case, seconds, side=512):
+    """The FP64 oracle on a bounded sample of the workload: a side x side
+    window of the same initial field (centred on the interface, walls at its
+    y ends), timed for about `seconds` of host time."""
+    import oracle
+
+    n = case.params.nx
+    y0 = n // 2 - side // 2
+    x0 = n // 2 - side // 2
+    sub = case.params.with_(nx=side, ny=side, precision=W.PREC_FP64)
+    phi = np.ascontiguousarray(case.phi[y0:y0 + side, x0:x0 + side])
+    o = oracle.Oracle(sub)
+    o.init_fields(phi)
+    o.step(1)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        o.step(2)
+        steps += 2
+    dt = time.perf_counter() - t0
+    return {"value": side * side * steps / dt / 1e6, "unit": UNIT, "cores": oracle.get_threads(),
+            "kind": "oracle",
+            "sample": f"{side}x{side} window of the {n}x{n} initial field at the interface, "
+                      f"{steps} FP64 steps ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle on the host cores, each step one oracle
+    time step of a 256 x 256 window of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    side = 256
+    n = args.n
+    full = W.rti_multimode(n, precision=W.PREC_FP64)
+    y0 = x0 = n // 2 - side // 2
+    case = W.Case("rti_window", full.params.with_(nx=side, ny=side),
+                  np.ascontiguousarray(full.phi[y0:y0 + side, x0:x0 + side]))
+    del full
+    o = oracle.Oracle(case.params)
+    o.init_fields(case.phi)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = side * side * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(n), "precision": "fp64", "sample_side": side},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                             "sample": f"{side}x{side} RTI window with the workload's parameters, "
+                                       f"{args.steps} timed FP64 steps"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2111_00847_gb300 as pk
+
+    prec = W.PREC_FP32 if args.precision == "fp32" else W.PREC_FP64
+    esize = 4 if prec == W.PREC_FP32 else 8
+    n = args.n
+    case = W.rti_multimode(n, precision=prec)
+    N = n * n
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    stream = torch.cuda.current_stream(dev)
+    sim = pk.Simulation(case.params, stream=stream)
+    sim.init_fields(case.phi)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ms)
+    sec = ms / 1e3
+    value = world * N * args.steps / sec / 1e6
+    per_launch = sec / args.steps
+
+    # ---- roofline of the dominant kernel (the fused step, one launch per step)
+    peak, peak_src = measured_peak()
+    alg_bytes = VALUES_PER_LU * esize * N
+    achieved = alg_bytes / per_launch / 1e9
+    tr_lu, tr_src = profiled_traffic(esize)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": (tr_lu * N if tr_lu is not None else None),
+                "peak_source": peak_src, "algorithmic_bytes_per_lu": VALUES_PER_LU * esize,
+                "traffic_source": tr_src}
+
+    # ---- end to end through the public API, host buffers, copies inside
+    e2e = None
+    if not args.no_e2e:
+        phi_h = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        phi_h.numpy()[...] = case.phi
+        out_h = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.init_fields(phi_h.numpy())
+        sim.step(args.steps)
+        sim.fields(pk.LBM_PHI, out=out_h.numpy())
+        torch.cuda.synchronize()
+        te = max_over_ranks(time.perf_counter() - t0)
+        barrier()
+        e2e = {"value": world * N * args.steps / te / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": 8 * N / args.steps, "d2h_bytes_per_step": 8 * N / args.steps,
+               "what": "lbm_init_fields(phi from pinned host) + lbm_step(K) + lbm_fields(PHI to pinned host)"}
+        del phi_h, out_h
+    state_gb = sim.device_bytes / 1e9
+    sim.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(case, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if esize == 4 else "f64",
+                "data": "synthetic",
+                "config": {"workload": workload_name(n), "nx": n, "ny": n,
+                           "precision": args.precision, "phase_model": "AC", "flux": "present",
+                           "replicas": world, "parallelism": f"replicas{world}",
+                           "l2": f"inputs larger than L2 (device state {state_gb:.1f} GB)"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": args.steps, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

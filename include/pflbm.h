@@ -1,0 +1,207 @@
+/*
+ * pflbm.h -- C-ABI of the GB300 phase-field lattice Boltzmann library.
+ *
+ * The library advances the consistent and conservative phase-field lattice
+ * Boltzmann method of Zhan, Chai & Shi (arXiv:2111.00847) on one CUDA
+ * device.  One time step t -> t+1 over the whole grid is one launch of a
+ * fused kernel that pulls the D2Q9 populations f_i (phase field) and g_i
+ * (hydrodynamics), evaluates phi = sum_i f_i on a halo ring, the isotropic
+ * stencils of Eqs. (C.9)-(C.10), the chemical potential (Eq. (5)), the
+ * Allen-Cahn (Eq. (7)) or Cahn-Hilliard (Eq. (6)) diffusion flux, the
+ * consistent mass flux m^{phi C} (Eq. (15)), velocity (Eq. (22b)) and pressure
+ * (Eq. (39), second way of Remark 1), and both MRT collisions (Eqs. (17),
+ * (40)) with the moment vectors of Eqs. (C.2)-(C.4), then stores the
+ * post-collision populations for the next pull.
+ *
+ * Conventions shared by every entry point
+ *  - Grid: nx x ny nodes, node (i, j) at (i + 1/2, j + 1/2); host fields are
+ *    row-major double arrays [ny][nx] (x fastest).  Population arrays are
+ *    [9][ny][nx] in the D2Q9 order c_0 = (0,0), c_1 = (1,0), c_2 = (0,1),
+ *    c_3 = (-1,0), c_4 = (0,-1), c_5 = (1,1), c_6 = (-1,1), c_7 = (-1,-1),
+ *    c_8 = (1,-1) (the order fixed by the matrix of Eq. (C.1)).
+ *  - Boundaries: each side is periodic or a half-way bounce-back wall (no
+ *    slip for g, no flux for f, Sec. 4) with the wetting condition of
+ *    Eqs. (49)-(50) at the contact angle of that side.
+ *  - Return codes: LBM_OK (0) or a negative LBM_E* code; nothing aborts and
+ *    no entry point throws.  lbm_last_error() describes the last failure.
+ *  - Threading: a handle is not re-entrant; calls on one handle must not
+ *    overlap.  Different handles are independent.
+ *  - Streams: all device work of a handle runs on the CUDA stream given to
+ *    lbm_create (NULL: the legacy default stream).  lbm_step is asynchronous
+ *    unless diagnostics are due; lbm_init_fields, lbm_fields and
+ *    lbm_set_fields synchronise the stream before returning.
+ */
+#ifndef PFLBM_H
+#define PFLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ABI_VERSION 1
+#define LBM_NDIAG 8
+
+/* return codes */
+enum {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,       /* bad argument or parameter (message in lbm_last_error) */
+    LBM_ENOMEM = -2,       /* device or host allocation failed */
+    LBM_ECUDA = -3,        /* a CUDA call failed (message names the call) */
+    LBM_EUNSTABLE = -4,    /* diagnostics found a non-finite value or |u| > 0.4 */
+    LBM_EUNSUPPORTED = -5  /* valid but not implemented in this build */
+};
+
+/* lbm_params.precision: storage and arithmetic type of the populations */
+enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16_DEV = 2, LBM_BF16_DEV = 3 };
+/* lbm_params.phase_model: D(phi) of Eq. (1) */
+enum { LBM_AC = 0 /* Eq. (7), conservative Allen-Cahn */, LBM_CH = 1 /* Eq. (6), Cahn-Hilliard */ };
+/* lbm_params.flux_model (Sec. 4): present = consistent flux rho u + m^{phi C};
+ * original = m = rho u */
+enum { LBM_PRESENT = 0, LBM_ORIGINAL = 1, LBM_CORRECTED = 2 };
+/* lbm_params.visc_law: Eq. (11) (linear dynamic viscosity) or Eq. (12) */
+enum { LBM_LINEAR_MU = 0, LBM_INVERSE_NU = 1 };
+/* lbm_params.gravity_mode: body force G added to F = mu_phi grad phi + G
+ *   CONST: G = (gx, gy)                         (Sec. 4.2)
+ *   RHO:   G = rho (gx, gy)                     (Sec. 4.5)
+ *   RHO_MINUS_MEAN: G = (rho - (rhoA+rhoB)/2) (gx, gy)   (Sec. 4.4) */
+enum { LBM_G_CONST = 0, LBM_G_RHO = 1, LBM_G_RHO_MINUS_MEAN = 2 };
+/* lbm_params.bc[side] */
+enum { LBM_PERIODIC = 0, LBM_WALL = 1 };
+enum { LBM_LEFT = 0, LBM_RIGHT = 1, LBM_BOTTOM = 2, LBM_TOP = 3 };
+/* lbm_fields / lbm_set_fields selector */
+enum {
+    LBM_PHI = 0,   /* order parameter phi = sum_i f_i          [ny][nx]    */
+    LBM_UX = 1,    /* velocity u, Eq. (22b)                    [ny][nx]    */
+    LBM_UY = 2,    /* velocity v                               [ny][nx]    */
+    LBM_P = 3,     /* pressure p, Eq. (39)                     [ny][nx]    */
+    LBM_RHO = 4,   /* density rho(phi), Eq. (10)               [ny][nx]    */
+    LBM_F_POP = 5, /* f_i(x, t) as seen by each node           [9][ny][nx] */
+    LBM_G_POP = 6, /* g_i(x, t) as seen by each node           [9][ny][nx] */
+    LBM_HIST = 7,  /* chi(t-1): phi u, phi v, u.m, u mx - v my, u my + v mx  [5][ny][nx] */
+    LBM_DIAG = 8,  /* last diagnostics record                  [LBM_NDIAG] */
+    LBM_MU = 9,    /* chemical potential mu_phi, Eq. (5)       [ny][nx]    */
+    LBM_MCX = 10,  /* m^{phi C} x, Eq. (15)                    [ny][nx]    */
+    LBM_MCY = 11   /* m^{phi C} y                              [ny][nx]    */
+};
+
+/*
+ * Problem parameters, in the terms the paper states the problem (lattice
+ * units, dx = dt = 1, c_s^2 = 1/3).
+ *  version      must be LBM_ABI_VERSION
+ *  nx, ny       grid size, each >= 3, nx*ny < 2^31
+ *  phiA > phiB  order parameter of the two bulk phases (AC: 1, 0; CH: 1, -1)
+ *  rhoA, rhoB   densities; rho(phi) linear, Eq. (10)
+ *  muA, muB     dynamic viscosities; nu = mu / rho
+ *  mobility     M_phi
+ *  width        interface width W;  sigma  surface tension (Eq. (3) gives beta, k)
+ *  eta          adjustable constant of Eqs. (C.3)-(C.4); 1 is the paper's value
+ *  gx, gy       gravity / body-force vector, see gravity_mode
+ *  rho0         constant of alpha_0 in Eq. (19)
+ *  theta_deg    contact angle of each side (used where bc == LBM_WALL)
+ *  s_f, s_g     MRT relaxation rates; NaN selects the default of Sec. 4:
+ *               s_f^3 = s_f^5 = 1/(M_phi/(eta c_s^2) + 1/2),
+ *               s_g^7 = s_g^8 = 1/(nu(phi)/c_s^2 + 1/2) per node, others 1
+ *  diag_every   if > 0, lbm_step computes the diagnostics every diag_every
+ *               steps (and then synchronises) and fails with LBM_EUNSTABLE
+ *               on a non-finite value or |u| > 0.4
+ */
+typedef struct lbm_params {
+    int32_t version, nx, ny, precision;
+    int32_t phase_model, flux_model, visc_law, gravity_mode;
+    int32_t bc[4];
+    int32_t diag_every, reserved;
+    double phiA, phiB, rhoA, rhoB, muA, muB;
+    double mobility, width, sigma, eta;
+    double gx, gy, rho0;
+    double theta_deg[4];
+    double s_f[9], s_g[9];
+} lbm_params;
+
+typedef struct lbm_handle lbm_handle;
+
+/*
+ * Optional device-memory provider.  alloc(bytes, stream, ctx) returns device
+ * memory of at least `bytes` bytes aligned to 256 bytes, or NULL on failure;
+ * free(ptr, stream, ctx) releases it.  The Python binding passes PyTorch's
+ * caching allocator here.  NULL: the library calls cudaMalloc / cudaFree.
+ */
+typedef struct lbm_allocator {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, void *stream, void *ctx);
+    void *ctx;
+} lbm_allocator;
+
+/*
+ * Create a simulation on the current CUDA device.
+ *  params  validated here (LBM_EINVAL with a message on any bad field;
+ *          LBM_EUNSUPPORTED for flux_model == LBM_CORRECTED)
+ *  stream  cudaStream_t to run on, or NULL
+ *  alloc   device-memory provider or NULL
+ *  out     receives the handle (NULL on failure)
+ * Device memory owned by the handle: 2 x 18 population planes + 5 history
+ * planes of the storage type, plus work planes created on first use by
+ * lbm_fields / diagnostics.  All of it is released by lbm_destroy.
+ */
+int lbm_create(const lbm_params *params, void *stream, const lbm_allocator *alloc,
+               lbm_handle **out);
+
+/*
+ * Set the state at t = 0 from host fields (row-major [ny][nx] doubles, read
+ * only during the call; ux, uy, p may be NULL for zero).  Reading of the
+ * paper (which states no initial populations): f = f^eq(phi, u),
+ * g = g^eq(p, u) with m^{phi C} of phi, then the history is set to the
+ * values the scheme computes at t = 0, so the first step's time derivatives
+ * vanish.
+ */
+int lbm_init_fields(lbm_handle *h, const double *phi, const double *ux, const double *uy,
+                    const double *p);
+
+/* Advance nsteps (>= 0) time steps.  Asynchronous on the handle's stream
+ * except at diagnostic points (diag_every > 0). */
+int lbm_step(lbm_handle *h, int64_t nsteps);
+
+/*
+ * Copy a field at the current time to host memory `out` (layout per the
+ * selector; doubles).  Macroscopic fields are recomputed from the current
+ * populations by the step kernel's own formulas.  LBM_DIAG returns the
+ * diagnostics at the current time (computed now): t, sum phi, D_u^rms,
+ * S_m^rms (Eqs. (42)-(43), averaged over nodes not adjacent to a wall),
+ * max |u|, count of non-finite nodes, number of averaged nodes, 0.
+ * S_m^rms needs phi(t-1): it is exact at diagnostic points of lbm_step and
+ * at t = 0; elsewhere it uses the last recorded phi(t-1).
+ */
+int lbm_fields(lbm_handle *h, int32_t which, double *out);
+
+/* As lbm_fields, restricted to the node rectangle [x0, x0+w) x [y0, y0+hgt)
+ * (out: [planes][hgt][w] doubles).  Lets a caller sample a grid too large to
+ * copy whole.  A rectangle outside the grid: LBM_EINVAL.  LBM_DIAG ignores
+ * the rectangle. */
+int lbm_fields_region(lbm_handle *h, int32_t which, int32_t x0, int32_t y0, int32_t w, int32_t hgt,
+                      double *out);
+
+/* Overwrite LBM_F_POP, LBM_G_POP or LBM_HIST (layouts as in lbm_fields) from
+ * host doubles, e.g. to resume from a checkpoint.  Other selectors:
+ * LBM_EINVAL. */
+int lbm_set_fields(lbm_handle *h, int32_t which, const double *in);
+
+/* Number of time steps taken since lbm_init_fields. */
+int64_t lbm_time(const lbm_handle *h);
+
+/* Bytes of device memory the handle holds now. */
+int64_t lbm_device_bytes(const lbm_handle *h);
+
+/* Free the handle and all device memory it owns (NULL is ignored). */
+void lbm_destroy(lbm_handle *h);
+
+/* Message of the last failure on h (or of the last lbm_create failure when
+ * h is NULL).  Valid until the next call on the handle. */
+const char *lbm_last_error(const lbm_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFLBM_H */

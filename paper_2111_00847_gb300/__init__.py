@@ -1,0 +1,300 @@
+"""GB300-native consistent and conservative phase-field lattice Boltzmann.
+
+Python binding of the C-ABI library ``libpflbm.so`` (declared in
+``include/pflbm.h``).  This module only marshals arguments: every step of the
+method runs in the library's CUDA kernels.  PyTorch, when present, supplies
+the CUDA stream and the device memory (through its caching allocator); the
+library itself has no CPU path, and importing the binding without the built
+library, or creating a simulation without a CUDA device, raises.
+
+The functions ``lbm_create``, ``lbm_init_fields``, ``lbm_step``,
+``lbm_fields``, ``lbm_set_fields``, ``lbm_time``, ``lbm_device_bytes``,
+``lbm_destroy`` and ``lbm_last_error`` mirror the C entry points one to one;
+``Simulation`` wraps them with numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpflbm.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+LBM_FP64, LBM_FP32, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2, 3
+(LBM_PHI, LBM_UX, LBM_UY, LBM_P, LBM_RHO, LBM_F_POP, LBM_G_POP, LBM_HIST, LBM_DIAG, LBM_MU,
+ LBM_MCX, LBM_MCY) = range(12)
+LBM_NDIAG = 8
+LBM_ABI_VERSION = 1
+DIAG_KEYS = ("t", "sum_phi", "Du_rms", "Sm_rms", "umax", "nonfinite", "n_avg", "reserved")
+
+EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_fields", "lbm_fields_region",
+            "lbm_set_fields",
+            "lbm_time", "lbm_device_bytes", "lbm_destroy", "lbm_last_error")
+
+
+class LbmParams(C.Structure):
+    """ctypes image of ``lbm_params``."""
+
+    _fields_ = [
+        ("version", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("precision", C.c_int32),
+        ("phase_model", C.c_int32), ("flux_model", C.c_int32), ("visc_law", C.c_int32),
+        ("gravity_mode", C.c_int32), ("bc", C.c_int32 * 4), ("diag_every", C.c_int32),
+        ("reserved", C.c_int32),
+        ("phiA", C.c_double), ("phiB", C.c_double), ("rhoA", C.c_double), ("rhoB", C.c_double),
+        ("muA", C.c_double), ("muB", C.c_double), ("mobility", C.c_double), ("width", C.c_double),
+        ("sigma", C.c_double), ("eta", C.c_double), ("gx", C.c_double), ("gy", C.c_double),
+        ("rho0", C.c_double), ("theta_deg", C.c_double * 4), ("s_f", C.c_double * 9),
+        ("s_g", C.c_double * 9),
+    ]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class LbmAllocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -m paper_2111_00847_gb300.build` (there is no CPU fallback)")
+    L = C.CDLL(path)
+    dp = C.POINTER(C.c_double)
+    L.lbm_create.argtypes = [C.POINTER(LbmParams), C.c_void_p, C.POINTER(LbmAllocator),
+                             C.POINTER(C.c_void_p)]
+    L.lbm_create.restype = C.c_int
+    L.lbm_init_fields.argtypes = [C.c_void_p, dp, dp, dp, dp]
+    L.lbm_step.argtypes = [C.c_void_p, C.c_int64]
+    L.lbm_fields.argtypes = [C.c_void_p, C.c_int32, dp]
+    L.lbm_fields_region.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                    C.c_int32, dp]
+    L.lbm_set_fields.argtypes = [C.c_void_p, C.c_int32, dp]
+    L.lbm_time.argtypes = [C.c_void_p]
+    L.lbm_time.restype = C.c_int64
+    L.lbm_device_bytes.argtypes = [C.c_void_p]
+    L.lbm_device_bytes.restype = C.c_int64
+    L.lbm_destroy.argtypes = [C.c_void_p]
+    L.lbm_destroy.restype = None
+    L.lbm_last_error.argtypes = [C.c_void_p]
+    L.lbm_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def params_struct(prm) -> LbmParams:
+    """Fill ``lbm_params`` from any object with the parameter attributes
+    (e.g. ``workloads.Params``)."""
+    s = LbmParams()
+    s.version = LBM_ABI_VERSION
+    for name in ("nx", "ny", "precision", "phase_model", "flux_model", "visc_law",
+                 "gravity_mode", "diag_every"):
+        setattr(s, name, int(getattr(prm, name)))
+    for i in range(4):
+        s.bc[i] = int(prm.bc[i])
+        s.theta_deg[i] = float(prm.theta_deg[i])
+    for name in ("phiA", "phiB", "rhoA", "rhoB", "muA", "muB", "mobility", "width", "sigma",
+                 "eta", "gx", "gy", "rho0"):
+        setattr(s, name, float(getattr(prm, name)))
+    for k in range(9):
+        s.s_f[k] = float(prm.s_f[k])
+        s.s_g[k] = float(prm.s_g[k])
+    return s
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pflbm error {code}: {msg}")
+        self.code = code
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+# ---- one-to-one wrappers of the C entry points ------------------------------
+def lbm_last_error(handle=None) -> str:
+    return (load().lbm_last_error(handle) or b"").decode()
+
+
+def _check(rc: int, handle=None):
+    if rc != LBM_OK:
+        raise LbmError(rc, lbm_last_error(handle))
+
+
+def lbm_create(params: LbmParams, stream: int = 0, allocator: LbmAllocator | None = None):
+    h = C.c_void_p()
+    rc = load().lbm_create(C.byref(params), C.c_void_p(stream or None),
+                           C.byref(allocator) if allocator is not None else None, C.byref(h))
+    _check(rc)
+    return h
+
+
+def lbm_init_fields(h, phi, ux=None, uy=None, p=None):
+    _check(load().lbm_init_fields(h, _dptr(phi), _dptr(ux), _dptr(uy), _dptr(p)), h)
+
+
+def lbm_step(h, nsteps: int):
+    _check(load().lbm_step(h, int(nsteps)), h)
+
+
+def lbm_fields(h, which: int, out: np.ndarray):
+    _check(load().lbm_fields(h, int(which), _dptr(out)), h)
+
+
+def lbm_fields_region(h, which: int, x0: int, y0: int, w: int, hgt: int, out: np.ndarray):
+    _check(load().lbm_fields_region(h, int(which), int(x0), int(y0), int(w), int(hgt),
+                                    _dptr(out)), h)
+
+
+def lbm_set_fields(h, which: int, arr: np.ndarray):
+    _check(load().lbm_set_fields(h, int(which), _dptr(arr)), h)
+
+
+def lbm_time(h) -> int:
+    return int(load().lbm_time(h))
+
+
+def lbm_device_bytes(h) -> int:
+    return int(load().lbm_device_bytes(h))
+
+
+def lbm_destroy(h):
+    load().lbm_destroy(h)
+
+
+# ---- PyTorch plumbing --------------------------------------------------------
+def _torch():
+    try:
+        import torch
+    except ImportError:  # the library works without torch (own cudaMalloc)
+        return None
+    return torch if torch.cuda.is_available() else None
+
+
+def torch_allocator():
+    """An ``lbm_allocator`` drawing device memory from PyTorch's caching
+    allocator (returns (struct, keep-alive tuple))."""
+    torch = _torch()
+    if torch is None:
+        return None, ()
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0)))
+        except RuntimeError:
+            return None
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+    return LbmAllocator(a, f, None), (a, f)
+
+
+class Simulation:
+    """One simulation on the current CUDA device.
+
+    params: any object with the fields of ``lbm_params`` (``workloads.Params``).
+    stream: a ``torch.cuda.Stream`` or raw ``cudaStream_t`` integer; default is
+    PyTorch's current stream when PyTorch is available.
+    """
+
+    def __init__(self, params, stream=None, use_torch_allocator: bool = True):
+        self.params = params
+        self.nx, self.ny = int(params.nx), int(params.ny)
+        torch = _torch()
+        if stream is None and torch is not None:
+            stream = torch.cuda.current_stream()
+        self.stream_obj = stream
+        self.stream = int(getattr(stream, "cuda_stream", stream) or 0)
+        self._alloc, self._keep = (torch_allocator() if use_torch_allocator else (None, ()))
+        self._p = params_struct(params)
+        self._h = lbm_create(self._p, self.stream, self._alloc)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _field(self, a):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+        if a.shape != (self.ny, self.nx):
+            raise ValueError(f"field shape {a.shape} != {(self.ny, self.nx)}")
+        return a
+
+    def init_fields(self, phi, ux=None, uy=None, p=None):
+        arrs = [self._field(x) for x in (phi, ux, uy, p)]
+        lbm_init_fields(self._h, *arrs)
+
+    def step(self, n: int = 1):
+        lbm_step(self._h, n)
+
+    @property
+    def t(self) -> int:
+        return lbm_time(self._h)
+
+    @property
+    def device_bytes(self) -> int:
+        return lbm_device_bytes(self._h)
+
+    def fields(self, which: int, region=None, out: np.ndarray | None = None) -> np.ndarray:
+        """Field `which` at the current time; region = (x0, y0, w, h) limits it
+        to a node rectangle; `out` may supply the destination (float64,
+        C-contiguous, e.g. a view of pinned host memory)."""
+        x0, y0, w, hgt = region if region is not None else (0, 0, self.nx, self.ny)
+        if which in (LBM_F_POP, LBM_G_POP):
+            shape = (9, hgt, w)
+        elif which == LBM_HIST:
+            shape = (5, hgt, w)
+        elif which == LBM_DIAG:
+            shape = (LBM_NDIAG,)
+        else:
+            shape = (hgt, w)
+        if out is None:
+            out = np.empty(shape)
+        elif out.shape != shape or out.dtype != np.float64 or not out.flags.c_contiguous:
+            raise ValueError(f"out must be a C-contiguous float64 array of shape {shape}")
+        lbm_fields_region(self._h, which, x0, y0, w, hgt, out)
+        return out
+
+    def set_fields(self, which: int, arr):
+        a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64))
+        lbm_set_fields(self._h, which, a)
+
+    def diag(self) -> dict:
+        return dict(zip(DIAG_KEYS, self.fields(LBM_DIAG).tolist()))
+
+
+__all__ = ["Simulation", "LbmParams", "LbmError", "load", "params_struct", "torch_allocator",
+           *EXPORTED]

@@ -1,0 +1,511 @@
+// C-ABI of the GB300 phase-field lattice Boltzmann library (include/pflbm.h).
+//
+// Host side only: parameter validation, device memory (own cudaMalloc or a
+// caller-supplied allocator), the per-run constants handed to the kernels,
+// and the sequencing of launches on the handle's stream.  Every step of the
+// method runs in the device kernels of pflbm_kernels.cuh.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pflbm.h"
+#include "pflbm_launch.h"
+
+using namespace pflbm;
+
+struct lbm_handle {
+  lbm_params prm;
+  cudaStream_t stream = nullptr;
+  lbm_allocator alloc{};
+  bool have_alloc = false;
+  int prec = LBM_FP64;
+  size_t esize = 8;
+  int nx = 0, ny = 0, pitch = 0;
+  long long plane = 0;
+  void* pops[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [f|g][A|B]
+  int cur = 0;
+  void* hist = nullptr;
+  void* phi_prev = nullptr;
+  void* macro = nullptr;
+  double* dstage = nullptr;
+  int dstage_planes = 0;
+  double* dpart = nullptr;
+  double* ddiag = nullptr;
+  int nparts = 0;
+  double diag[LBM_NDIAG] = {0};
+  int64_t t = 0;
+  int64_t bytes = 0;
+  std::vector<std::pair<void*, size_t>> blocks;
+  std::string err;
+  // derived constants (double)
+  double beta, kappa, lam_coef, drho, sf[9], sg[9], H;
+  bool sg_node[9];
+  double wa[4];
+};
+
+static std::string g_create_error;
+
+static int fail(lbm_handle* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  else g_create_error = buf;
+  return code;
+}
+
+#define CUDA_TRY(h, call)                                                                          \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return fail((h), e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s (%s)",    \
+                  #call, cudaGetErrorString(e_), cudaGetErrorName(e_));                            \
+  } while (0)
+
+static void* dev_alloc(lbm_handle* h, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 256;
+  if (h->have_alloc) {
+    p = h->alloc.alloc(bytes, (void*)h->stream, h->alloc.ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) {
+    h->blocks.emplace_back(p, bytes);
+    h->bytes += (int64_t)bytes;
+  }
+  return p;
+}
+
+static void dev_free(lbm_handle* h, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < h->blocks.size(); ++i)
+    if (h->blocks[i].first == p) {
+      h->bytes -= (int64_t)h->blocks[i].second;
+      h->blocks.erase(h->blocks.begin() + i);
+      break;
+    }
+  if (h->have_alloc) h->alloc.free(p, (void*)h->stream, h->alloc.ctx);
+  else cudaFree(p);
+}
+
+static double cos_deg(double th) { return th == 90.0 ? 0.0 : std::cos(th * 3.14159265358979323846 / 180.0); }
+
+static int validate(const lbm_params* P) {
+  if (!P) return fail(nullptr, LBM_EINVAL, "params is NULL");
+  if (P->version != LBM_ABI_VERSION) return fail(nullptr, LBM_EINVAL, "params.version %d != %d", P->version, LBM_ABI_VERSION);
+  if (P->nx < 3 || P->ny < 3) return fail(nullptr, LBM_EINVAL, "grid %d x %d: each side must be >= 3", P->nx, P->ny);
+  const long long pitch = ((long long)P->nx + 31) / 32 * 32;
+  if (P->ny > 65535) return fail(nullptr, LBM_EINVAL, "ny = %d exceeds 65535", P->ny);
+  if (pitch * P->ny >= (1LL << 31)) return fail(nullptr, LBM_EINVAL, "grid %d x %d too large (pitch*ny must be < 2^31)", P->nx, P->ny);
+  if (P->precision == LBM_FP16_DEV || P->precision == LBM_BF16_DEV)
+    return fail(nullptr, LBM_EUNSUPPORTED, "reduced-precision storage is not built in this library");
+  if (P->precision != LBM_FP64 && P->precision != LBM_FP32) return fail(nullptr, LBM_EINVAL, "precision %d", P->precision);
+  if (P->phase_model != LBM_AC && P->phase_model != LBM_CH) return fail(nullptr, LBM_EINVAL, "phase_model %d", P->phase_model);
+  if (P->flux_model == LBM_CORRECTED) return fail(nullptr, LBM_EUNSUPPORTED, "flux_model CORRECTED is not built in this library");
+  if (P->flux_model != LBM_PRESENT && P->flux_model != LBM_ORIGINAL) return fail(nullptr, LBM_EINVAL, "flux_model %d", P->flux_model);
+  if (P->visc_law != LBM_LINEAR_MU && P->visc_law != LBM_INVERSE_NU) return fail(nullptr, LBM_EINVAL, "visc_law %d", P->visc_law);
+  if (P->gravity_mode < 0 || P->gravity_mode > 2) return fail(nullptr, LBM_EINVAL, "gravity_mode %d", P->gravity_mode);
+  if (P->bc[0] != P->bc[1] || P->bc[2] != P->bc[3]) return fail(nullptr, LBM_EINVAL, "opposite sides must share a boundary type");
+  for (int s = 0; s < 4; ++s) {
+    if (P->bc[s] != LBM_PERIODIC && P->bc[s] != LBM_WALL) return fail(nullptr, LBM_EINVAL, "bc[%d] = %d", s, P->bc[s]);
+    if (!(P->theta_deg[s] >= 0.0 && P->theta_deg[s] <= 180.0)) return fail(nullptr, LBM_EINVAL, "theta_deg[%d] outside [0, 180]", s);
+  }
+  if (!(P->phiA > P->phiB)) return fail(nullptr, LBM_EINVAL, "phiA must exceed phiB");
+  if (!(P->rhoA > 0 && P->rhoB > 0 && P->muA > 0 && P->muB > 0)) return fail(nullptr, LBM_EINVAL, "densities and viscosities must be positive");
+  if (!(P->width > 0 && P->sigma >= 0 && P->mobility >= 0 && P->eta > 0)) return fail(nullptr, LBM_EINVAL, "width > 0, sigma >= 0, mobility >= 0, eta > 0 required");
+  for (int k = 0; k < 9; ++k) {
+    if (!std::isnan(P->s_f[k]) && !(P->s_f[k] > 0 && P->s_f[k] < 2)) return fail(nullptr, LBM_EINVAL, "s_f[%d] outside (0, 2)", k);
+    if (!std::isnan(P->s_g[k]) && !(P->s_g[k] > 0 && P->s_g[k] < 2)) return fail(nullptr, LBM_EINVAL, "s_g[%d] outside (0, 2)", k);
+  }
+  const double amax = 4.0 / (P->width * (P->phiA - P->phiB));
+  if (8.0 / 3.0 - amax * std::fabs(P->phiA + P->phiB) <= 0.0) return fail(nullptr, LBM_EINVAL, "interface width too small for the wetting root");
+  if (P->diag_every < 0) return fail(nullptr, LBM_EINVAL, "diag_every < 0");
+  return LBM_OK;
+}
+
+static void derive(lbm_handle* h) {
+  const lbm_params& P = h->prm;
+  const double dphi = P.phiA - P.phiB;
+  // Eq. (3), Eq. (8), Eq. (10)
+  h->beta = 12.0 * P.sigma / (P.width * dphi * dphi * dphi * dphi);
+  h->kappa = 1.5 * P.sigma * P.width / (dphi * dphi);
+  h->lam_coef = P.sigma > 0.0 ? std::sqrt(2.0 * h->beta / h->kappa) : 4.0 / (P.width * dphi);
+  h->drho = (P.rhoA - P.rhoB) / dphi;
+  // relaxation rates (Sec. 4): NaN -> default rule
+  for (int k = 0; k < 9; ++k) {
+    h->sf[k] = std::isnan(P.s_f[k]) ? ((k == 3 || k == 5) ? 1.0 / (3.0 * P.mobility / P.eta + 0.5) : 1.0) : P.s_f[k];
+    h->sg_node[k] = std::isnan(P.s_g[k]) && (k == 7 || k == 8);
+    h->sg[k] = std::isnan(P.s_g[k]) ? 1.0 : P.s_g[k];
+  }
+  // App. C: H = (s_g^2 - s_g^0) / (9 s_g^0 s_g^2)
+  h->H = (h->sg[2] - h->sg[0]) / (9.0 * h->sg[0] * h->sg[2]);
+  for (int s = 0; s < 4; ++s) h->wa[s] = 4.0 * cos_deg(P.theta_deg[s]) / (P.width * dphi);
+}
+
+template <typename T>
+static Phys<T> make_phys(const lbm_handle* h) {
+  const lbm_params& Q = h->prm;
+  Phys<T> P;
+  std::memset(&P, 0, sizeof(P));
+  P.nx = h->nx;
+  P.ny = h->ny;
+  P.pitch = h->pitch;
+  P.plane = h->plane;
+  P.wall_x = Q.bc[LBM_LEFT] == LBM_WALL;
+  P.wall_y = Q.bc[LBM_BOTTOM] == LBM_WALL;
+  P.gravity_mode = Q.gravity_mode;
+  P.visc_inverse = Q.visc_law == LBM_INVERSE_NU;
+  P.sg7_node = h->sg_node[7];
+  P.sg8_node = h->sg_node[8];
+  P.phiA = T(Q.phiA);
+  P.phiB = T(Q.phiB);
+  P.phibar = T(0.5 * (Q.phiA + Q.phiB));
+  P.inv_dphi = T(1.0 / (Q.phiA - Q.phiB));
+  P.beta4 = T(4.0 * h->beta);
+  P.kappa = T(h->kappa);
+  P.lam_coef = T(h->lam_coef);
+  P.drho = T(h->drho);
+  P.rhoB = T(Q.rhoB);
+  P.rho_mean = T(0.5 * (Q.rhoA + Q.rhoB));
+  P.mob_drho = Q.flux_model == LBM_PRESENT ? T(h->drho * Q.mobility) : T(0);
+  P.muA = T(Q.muA);
+  P.muB = T(Q.muB);
+  P.inuA = T(Q.rhoA / Q.muA);
+  P.inuB = T(Q.rhoB / Q.muB);
+  P.gx = T(Q.gx);
+  P.gy = T(Q.gy);
+  P.eta = T(Q.eta);
+  P.H = T(h->H);
+  P.K = T(1.0 / 3.0);
+  for (int k = 0; k < 9; ++k) {
+    P.sf[k] = T(h->sf[k]);
+    P.hf[k] = T(1.0 - 0.5 * h->sf[k]);
+    P.sg[k] = T(h->sg[k]);
+    P.hg[k] = T(1.0 - 0.5 * h->sg[k]);
+  }
+  for (int s = 0; s < 4; ++s) P.wa[s] = T(h->wa[s]);
+  return P;
+}
+
+// ---------------------------------------------------------------------------
+// Typed operations (T = float or double)
+// ---------------------------------------------------------------------------
+template <typename T>
+static Bufs<T> bufs_now(lbm_handle* h) {
+  Bufs<T> B;
+  std::memset(&B, 0, sizeof(B));
+  B.fin = (const T*)h->pops[0][h->cur];
+  B.gin = (const T*)h->pops[1][h->cur];
+  B.fout = (T*)h->pops[0][1 - h->cur];
+  B.gout = (T*)h->pops[1][1 - h->cur];
+  B.hist = (T*)h->hist;
+  B.macro = (T*)h->macro;
+  return B;
+}
+
+static int ensure_stage(lbm_handle* h, int planes) {
+  if (h->dstage_planes >= planes) return LBM_OK;
+  if (h->dstage) dev_free(h, h->dstage);
+  h->dstage = (double*)dev_alloc(h, (size_t)planes * h->nx * h->ny * sizeof(double));
+  h->dstage_planes = h->dstage ? planes : 0;
+  if (!h->dstage) return fail(h, LBM_ENOMEM, "staging buffer of %d planes", planes);
+  return LBM_OK;
+}
+
+static int ensure_macro(lbm_handle* h) {
+  if (h->macro) return LBM_OK;
+  h->macro = dev_alloc(h, (size_t)NMACRO * h->plane * h->esize);
+  if (!h->macro) return fail(h, LBM_ENOMEM, "macro planes");
+  return LBM_OK;
+}
+
+template <typename T>
+static int run_macro(lbm_handle* h) {
+  int rc = ensure_macro(h);
+  if (rc) return rc;
+  const Phys<T> P = make_phys<T>(h);
+  Bufs<T> B = bufs_now<T>(h);
+  B.macro = (T*)h->macro;
+  CUDA_TRY(h, launch_march<T>(h->prm.phase_model, MODE_MACRO, P, B, h->stream));
+  return LBM_OK;
+}
+
+template <typename T>
+static int run_diag(lbm_handle* h) {
+  int rc = run_macro<T>(h);
+  if (rc) return rc;
+  const Phys<T> P = make_phys<T>(h);
+  CUDA_TRY(h, launch_diag<T>(P, (const T*)h->macro, (const T*)h->phi_prev, h->dpart, h->nparts, h->ddiag, h->stream));
+  double r[DIAG_FIELDS];
+  CUDA_TRY(h, cudaMemcpyAsync(r, h->ddiag, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  const double n = r[5];
+  h->diag[0] = (double)h->t;
+  h->diag[1] = r[0];
+  h->diag[2] = n > 0 ? std::sqrt(r[1] / n) : 0.0;
+  h->diag[3] = n > 0 ? std::sqrt(r[2] / n) : 0.0;
+  h->diag[4] = r[3];
+  h->diag[5] = r[4];
+  h->diag[6] = n;
+  h->diag[7] = 0.0;
+  return LBM_OK;
+}
+
+template <typename T>
+static int do_step(lbm_handle* h, int64_t n) {
+  const Phys<T> P = make_phys<T>(h);
+  const int de = h->prm.diag_every;
+  for (int64_t s = 0; s < n; ++s) {
+    const bool due = de > 0 && ((h->t + 1) % de == 0);
+    Bufs<T> B = bufs_now<T>(h);
+    B.phi_prev = due ? (T*)h->phi_prev : nullptr;
+    CUDA_TRY(h, launch_march<T>(h->prm.phase_model, MODE_STEP, P, B, h->stream));
+    h->cur ^= 1;
+    h->t += 1;
+    if (due) {
+      int rc = run_diag<T>(h);
+      if (rc) return rc;
+      if (h->diag[5] > 0 || !(h->diag[4] <= 0.4))
+        return fail(h, LBM_EUNSTABLE, "unstable at t=%lld: %g non-finite nodes, max|u| = %g",
+                    (long long)h->t, h->diag[5], h->diag[4]);
+    }
+  }
+  CUDA_TRY(h, cudaGetLastError());
+  return LBM_OK;
+}
+
+template <typename T>
+static int do_init(lbm_handle* h, const double* phi, const double* ux, const double* uy, const double* p) {
+  const long long N = (long long)h->nx * h->ny;
+  const int planes = 1 + (ux ? 1 : 0) + (uy ? 1 : 0) + (p ? 1 : 0);
+  int rc = ensure_stage(h, planes);
+  if (rc) return rc;
+  const Phys<T> P = make_phys<T>(h);
+  Bufs<T> B = bufs_now<T>(h);
+  double* d = h->dstage;
+  CUDA_TRY(h, cudaMemcpyAsync(d, phi, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  B.iphi = d;
+  d += N;
+  if (ux) { CUDA_TRY(h, cudaMemcpyAsync(d, ux, N * sizeof(double), cudaMemcpyHostToDevice, h->stream)); B.iux = d; d += N; }
+  if (uy) { CUDA_TRY(h, cudaMemcpyAsync(d, uy, N * sizeof(double), cudaMemcpyHostToDevice, h->stream)); B.iuy = d; d += N; }
+  if (p) { CUDA_TRY(h, cudaMemcpyAsync(d, p, N * sizeof(double), cudaMemcpyHostToDevice, h->stream)); B.ip = d; d += N; }
+  // equilibria per node into the spare buffers, then scatter to the pull layout
+  CUDA_TRY(h, launch_march<T>(h->prm.phase_model, MODE_INIT, P, B, h->stream));
+  CUDA_TRY(h, launch_unstream<T>(P, (const T*)h->pops[0][1 - h->cur], (T*)h->pops[0][h->cur], h->stream));
+  CUDA_TRY(h, launch_unstream<T>(P, (const T*)h->pops[1][1 - h->cur], (T*)h->pops[1][h->cur], h->stream));
+  // history := chi(0), and phi(t-1) := phi(0)
+  Bufs<T> Bh = bufs_now<T>(h);
+  Bh.phi_prev = (T*)h->phi_prev;
+  CUDA_TRY(h, launch_march<T>(h->prm.phase_model, MODE_HIST, P, Bh, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->t = 0;
+  std::memset(h->diag, 0, sizeof(h->diag));
+  return LBM_OK;
+}
+
+struct Region {
+  int x0, y0, w, h;
+};
+
+template <typename T>
+static int export_planes(lbm_handle* h, const T* src, int planes, double add0, double* out, Region r) {
+  int rc = ensure_stage(h, 1);
+  if (rc) return rc;
+  const Phys<T> P = make_phys<T>(h);
+  const long long N = (long long)r.w * r.h;
+  for (int k = 0; k < planes; ++k) {
+    CUDA_TRY(h, launch_export<T>(P, src + (long long)k * h->plane, h->dstage, 1, k == 0 ? add0 : 0.0,
+                                 r.x0, r.y0, r.w, r.h, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(out + k * N, h->dstage, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+template <typename T>
+static int import_planes(lbm_handle* h, const double* in, int planes, double sub0, T* dst) {
+  int rc = ensure_stage(h, 1);
+  if (rc) return rc;
+  const Phys<T> P = make_phys<T>(h);
+  const long long N = (long long)h->nx * h->ny;
+  for (int k = 0; k < planes; ++k) {
+    CUDA_TRY(h, cudaMemcpyAsync(h->dstage, in + k * N, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, launch_import<T>(P, h->dstage, dst + (long long)k * h->plane, 1, k == 0 ? sub0 : 0.0, h->stream));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+template <typename T>
+static int do_fields(lbm_handle* h, int which, double* out, Region reg) {
+  const Phys<T> P = make_phys<T>(h);
+  switch (which) {
+    case LBM_F_POP:
+    case LBM_G_POP: {
+      const int s = which == LBM_F_POP ? 0 : 1;
+      T* scratch = (T*)h->pops[s][1 - h->cur];
+      CUDA_TRY(h, launch_pull<T>(P, (const T*)h->pops[s][h->cur], scratch, h->stream));
+      return export_planes<T>(h, scratch, 9, s == 1 ? h->prm.rho0 : 0.0, out, reg);
+    }
+    case LBM_HIST:
+      return export_planes<T>(h, (const T*)h->hist, 5, 0.0, out, reg);
+    case LBM_DIAG: {
+      int rc = run_diag<T>(h);
+      if (rc) return rc;
+      std::memcpy(out, h->diag, sizeof(h->diag));
+      return LBM_OK;
+    }
+    default:
+      break;
+  }
+  int plane;
+  switch (which) {
+    case LBM_PHI: plane = MAC_PHI; break;
+    case LBM_UX: plane = MAC_UX; break;
+    case LBM_UY: plane = MAC_UY; break;
+    case LBM_P: plane = MAC_P; break;
+    case LBM_RHO: plane = MAC_RHO; break;
+    case LBM_MU: plane = MAC_MU; break;
+    case LBM_MCX: plane = MAC_MCX; break;
+    case LBM_MCY: plane = MAC_MCY; break;
+    default: return fail(h, LBM_EINVAL, "unknown field selector %d", which);
+  }
+  int rc = run_macro<T>(h);
+  if (rc) return rc;
+  return export_planes<T>(h, (const T*)h->macro + (long long)plane * h->plane, 1, 0.0, out, reg);
+}
+
+template <typename T>
+static int do_set_fields(lbm_handle* h, int which, const double* in) {
+  const Phys<T> P = make_phys<T>(h);
+  switch (which) {
+    case LBM_F_POP:
+    case LBM_G_POP: {
+      const int s = which == LBM_F_POP ? 0 : 1;
+      T* scratch = (T*)h->pops[s][1 - h->cur];
+      int rc = import_planes<T>(h, in, 9, s == 1 ? h->prm.rho0 : 0.0, scratch);
+      if (rc) return rc;
+      CUDA_TRY(h, launch_unstream<T>(P, scratch, (T*)h->pops[s][h->cur], h->stream));
+      CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+      return LBM_OK;
+    }
+    case LBM_HIST:
+      return import_planes<T>(h, in, 5, 0.0, (T*)h->hist);
+    default:
+      return fail(h, LBM_EINVAL, "field %d cannot be set", which);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// C entry points
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int lbm_create(const lbm_params* params, void* stream, const lbm_allocator* alloc, lbm_handle** out) {
+  if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate(params);
+  if (rc) return rc;
+  if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, LBM_EINVAL, "allocator needs alloc and free");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(nullptr, LBM_ECUDA, "no CUDA device available");
+  }
+  lbm_handle* h = new (std::nothrow) lbm_handle();
+  if (!h) return fail(nullptr, LBM_ENOMEM, "host allocation");
+  h->prm = *params;
+  h->stream = (cudaStream_t)stream;
+  if (alloc) {
+    h->alloc = *alloc;
+    h->have_alloc = true;
+  }
+  h->prec = params->precision;
+  h->esize = h->prec == LBM_FP64 ? 8 : 4;
+  h->nx = params->nx;
+  h->ny = params->ny;
+  h->pitch = (h->nx + 31) / 32 * 32;
+  h->plane = (long long)h->pitch * h->ny;
+  derive(h);
+  const size_t pl = (size_t)h->plane * h->esize;
+  bool ok = true;
+  for (int s = 0; s < 2; ++s)
+    for (int b = 0; b < 2; ++b) ok = ok && (h->pops[s][b] = dev_alloc(h, 9 * pl));
+  ok = ok && (h->hist = dev_alloc(h, 5 * pl));
+  ok = ok && (h->phi_prev = dev_alloc(h, pl));
+  const long long N = (long long)h->nx * h->ny;
+  h->nparts = (int)std::min<long long>((N + DIAG_THREADS - 1) / DIAG_THREADS, 152 * 8);
+  ok = ok && (h->dpart = (double*)dev_alloc(h, (size_t)h->nparts * DIAG_FIELDS * sizeof(double)));
+  ok = ok && (h->ddiag = (double*)dev_alloc(h, DIAG_FIELDS * sizeof(double)));
+  if (!ok) {
+    std::string msg = "device allocation of " + std::to_string(h->bytes) + " bytes failed";
+    lbm_destroy(h);
+    return fail(nullptr, LBM_ENOMEM, "%s", msg.c_str());
+  }
+  // zero the state so that a step before lbm_init_fields is well defined
+  for (auto& b : h->blocks) cudaMemsetAsync(b.first, 0, b.second, h->stream);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaError_t e = cudaGetLastError();
+    lbm_destroy(h);
+    return fail(nullptr, LBM_ECUDA, "initial memset: %s", cudaGetErrorString(e));
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_init_fields(lbm_handle* h, const double* phi, const double* ux, const double* uy, const double* p) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!phi) return fail(h, LBM_EINVAL, "phi is NULL");
+  return h->prec == LBM_FP64 ? do_init<double>(h, phi, ux, uy, p) : do_init<float>(h, phi, ux, uy, p);
+}
+
+int lbm_step(lbm_handle* h, int64_t nsteps) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps < 0");
+  return h->prec == LBM_FP64 ? do_step<double>(h, nsteps) : do_step<float>(h, nsteps);
+}
+
+int lbm_fields_region(lbm_handle* h, int32_t which, int32_t x0, int32_t y0, int32_t w, int32_t hgt,
+                      double* out) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!out) return fail(h, LBM_EINVAL, "out is NULL");
+  if (x0 < 0 || y0 < 0 || w < 1 || hgt < 1 || (long long)x0 + w > h->nx || (long long)y0 + hgt > h->ny)
+    return fail(h, LBM_EINVAL, "region [%d,%d)x[%d,%d) outside the %d x %d grid", x0, x0 + w, y0, y0 + hgt,
+                h->nx, h->ny);
+  const Region r{x0, y0, w, hgt};
+  return h->prec == LBM_FP64 ? do_fields<double>(h, which, out, r) : do_fields<float>(h, which, out, r);
+}
+
+int lbm_fields(lbm_handle* h, int32_t which, double* out) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  return lbm_fields_region(h, which, 0, 0, h->nx, h->ny, out);
+}
+
+int lbm_set_fields(lbm_handle* h, int32_t which, const double* in) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!in) return fail(h, LBM_EINVAL, "in is NULL");
+  return h->prec == LBM_FP64 ? do_set_fields<double>(h, which, in) : do_set_fields<float>(h, which, in);
+}
+
+int64_t lbm_time(const lbm_handle* h) { return h ? h->t : -1; }
+
+int64_t lbm_device_bytes(const lbm_handle* h) { return h ? h->bytes : 0; }
+
+void lbm_destroy(lbm_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  while (!h->blocks.empty()) dev_free(h, h->blocks.back().first);
+  delete h;
+}
+
+const char* lbm_last_error(const lbm_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,780 @@
+// Device code of the GB300 phase-field lattice Boltzmann path.
+//
+// Method: Zhan, Chai & Shi, "Consistent and conservative phase-field based
+// lattice Boltzmann method for incompressible two-phase flows"
+// (arXiv:2111.00847), Sec. 3 and App. C.  One launch of k_march<T, MODEL,
+// MODE_STEP> advances the whole grid by one time step.
+//
+// Memory layout (HBM).  Populations are structure-of-arrays planes
+// pop[i][y][pitch] (x fastest, pitch a multiple of 32 elements), one plane
+// per D2Q9 direction, two copies (A/B) per population set.  A plane holds
+// the POST-COLLISION value of each node (what it sends); the next step pulls
+// f_i(x) = f_i*(x - c_i) from it, or the reflected f_{opp(i)}*(x) where
+// x - c_i lies beyond a half-way bounce-back wall.  The hydrodynamic g_0 is
+// stored minus the constant rho0 of Eq. (19): rho0 is an eigen-direction of
+// the collision (M (rho0 e_0) = rho0 (1,-4,4,0,...)), so it passes through
+// unchanged and only costs FP32 precision if kept in g_0.  Five history
+// planes hold chi(t-1) for the explicit-Euler time derivatives of App. C.
+//
+// Kernel shape (k_march).  A block of BX threads owns an x-strip of BX
+// columns and marches up a y-segment of LY rows; one thread per column.
+// phi = sum_i f_i of a row is formed once, from the pulled populations the
+// thread keeps in registers for that row's collision one (AC) or two (CH)
+// iterations later, and parked in a shared-memory ring of rows, so the
+// isotropic stencils read every phi from shared memory; the only redundant
+// global traffic is the two halo columns per row (L2 hits: the neighbouring
+// strips march alongside) and the R look-ahead rows at each segment start.
+// Per lattice update the kernel reads 18 populations + 5 history values and
+// writes the same: 46 values, the algorithmic minimum of a fused step.
+//
+// No tensor cores: the step is a bandwidth-bound stencil with ~500 flops per
+// node and no dense contraction.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pflbm {
+
+enum { MODEL_AC = 0, MODEL_CH = 1 };
+// k_march modes:
+//  STEP : pull, collide, store populations + history (+ phi(t) when asked)
+//  MACRO: pull, write the macroscopic fields of time t (no state change)
+//  HIST : pull, write the history chi(t) only (set-up after init / resume)
+//  INIT : phi, u, p from device doubles; write f^eq, g^eq per node
+enum { MODE_STEP = 0, MODE_MACRO = 1, MODE_HIST = 2, MODE_INIT = 3 };
+enum {
+  MAC_PHI = 0, MAC_UX, MAC_UY, MAC_P, MAC_RHO, MAC_MU, MAC_MCX, MAC_MCY, MAC_TRS, NMACRO
+};
+enum { SIDE_LEFT = 0, SIDE_RIGHT = 1, SIDE_BOTTOM = 2, SIDE_TOP = 3 };
+
+constexpr int BX = 128;  // threads per block = columns per strip
+constexpr int LY = 64;   // rows per block
+constexpr int RING = 8;  // shared-memory ring of phi rows (power of two)
+
+// Per-run constants, in the arithmetic type.
+template <typename T>
+struct Phys {
+  int nx, ny, pitch;
+  long long plane;  // ny * pitch
+  int wall_x, wall_y;
+  int gravity_mode, visc_inverse, sg7_node, sg8_node;
+  T phiA, phiB, phibar, inv_dphi;
+  T beta4, kappa, lam_coef;  // 4 beta, k, sqrt(2 beta / k)   (Eqs. (3), (5), (8))
+  T drho, rhoB, rho_mean;    // d rho / d phi, rho_B, (rho_A + rho_B)/2
+  T mob_drho;                // (d rho/d phi) M_phi, zero for the original model
+  T muA, muB, inuA, inuB;    // mu_A, mu_B, 1/nu_A, 1/nu_B
+  T gx, gy, eta, H, K;
+  T sf[9], hf[9];            // s_f^k and 1 - s_f^k / 2
+  T sg[9], hg[9];
+  T wa[4];                   // a = 4 cos(theta) / (W dphi) per side, Eq. (50)
+};
+
+template <typename T>
+struct Bufs {
+  const T* fin;   // [9] planes, post-collision f of t-1
+  const T* gin;
+  T* fout;        // STEP: post-collision f of t;  INIT: f^eq per node
+  T* gout;
+  T* hist;        // [5] planes
+  T* macro;       // [NMACRO] planes (MACRO)
+  T* phi_prev;    // optional: phi(t) of the stepped time (STEP / HIST)
+  const double* iphi;  // INIT inputs, dense [ny][nx]
+  const double* iux;
+  const double* iuy;
+  const double* ip;
+};
+
+__host__ __device__ constexpr int slot_of(int r) { return (r + 2 * RING) & (RING - 1); }
+
+// ---------------------------------------------------------------------------
+// Pull the nine populations of node (x, r) from the post-collision planes,
+// with periodic wrap or half-way bounce-back at walls (Sec. 4).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void pull9(const T* __restrict__ buf, const Phys<T>& P, int x, int r,
+                                      T out[9]) {
+  int xm = x - 1, xp = x + 1, ym = r - 1, yp = r + 1;
+  bool bxm = false, bxp = false, bym = false, byp = false;
+  if (xm < 0) { if (P.wall_x) bxm = true; else xm += P.nx; }
+  if (xp >= P.nx) { if (P.wall_x) bxp = true; else xp -= P.nx; }
+  if (ym < 0) { if (P.wall_y) bym = true; else ym += P.ny; }
+  if (yp >= P.ny) { if (P.wall_y) byp = true; else yp -= P.ny; }
+  const long long pl = P.plane;
+  const long long rc = (long long)r * P.pitch, rm = (long long)ym * P.pitch,
+                  rp = (long long)yp * P.pitch;
+  const long long c = rc + x;
+  out[0] = buf[c];
+  out[1] = buf[bxm ? 3 * pl + c : 1 * pl + rc + xm];
+  out[2] = buf[bym ? 4 * pl + c : 2 * pl + rm + x];
+  out[3] = buf[bxp ? 1 * pl + c : 3 * pl + rc + xp];
+  out[4] = buf[byp ? 2 * pl + c : 4 * pl + rp + x];
+  out[5] = buf[(bxm || bym) ? 7 * pl + c : 5 * pl + rm + xm];
+  out[6] = buf[(bxp || bym) ? 8 * pl + c : 6 * pl + rm + xp];
+  out[7] = buf[(bxp || byp) ? 5 * pl + c : 7 * pl + rp + xp];
+  out[8] = buf[(bxm || byp) ? 6 * pl + c : 8 * pl + rp + xm];
+}
+
+template <typename T>
+__device__ __forceinline__ T sum9(const T v[9]) {
+  return ((v[0] + (v[1] + v[3])) + (v[2] + v[4])) + ((v[5] + v[7]) + (v[6] + v[8]));
+}
+
+// phi of the in-domain node (x, r) in a given mode.
+template <typename T, int MODE>
+__device__ __forceinline__ T phi_at(const Phys<T>& P, const Bufs<T>& B, int x, int r) {
+  if (MODE == MODE_INIT) {
+    return T(B.iphi[(long long)r * P.nx + x]);
+  } else {
+    T v[9];
+    pull9(B.fin, P, x, r, v);
+    return sum9(v);
+  }
+}
+
+// Wetting ghost, Eqs. (49)-(50): phi_w is the root the paper selects,
+// (-b + sqrt(b^2 - 4ac)) / (2a), evaluated as 2c / (-b - sqrt(b^2 - 4ac))
+// (the same number; finite as a -> 0, where it tends to -c/b); the ghost at
+// -1/2 is the quadratic through (0, phi_w), (1/2, phi_1), (3/2, phi_2).
+template <typename T>
+__device__ __forceinline__ T wall_ghost(const Phys<T>& P, int side, T phi1, T phi2) {
+  const T a = P.wa[side];
+  const T b = T(8.0 / 3.0) - a * (P.phiA + P.phiB);
+  const T c = a * P.phiA * P.phiB + phi2 * T(1.0 / 3.0) - T(3) * phi1;
+  T disc = b * b - T(4) * a * c;
+  disc = disc > T(0) ? disc : T(0);
+  const T phiw = T(2) * c / (-b - sqrt(disc));
+  return T(8.0 / 3.0) * phiw - T(2) * phi1 + phi2 * T(1.0 / 3.0);
+}
+
+// ---------------------------------------------------------------------------
+// Per-node update.  phi9 / mu9: values at x + c_i (D2Q9 order), f, g: pulled
+// populations, h: chi(t-1).  Writes the outputs of the mode.
+// ---------------------------------------------------------------------------
+template <typename T, int MODEL, int MODE>
+__device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, long long idx,
+                                            const T phi9[9], const T mu9[9], const T f[9],
+                                            const T g[9], const T h[5], T u_in, T v_in, T p_in) {
+  const T phi = phi9[0];
+  // isotropic gradient and Laplacian, Eqs. (C.9)-(C.10) (c_s^2 = 1/3):
+  // grad = 3 sum w_i c_i phi_i ; lap = 6 sum w_i (phi_i - phi)
+  const T gx = (phi9[1] - phi9[3]) * T(1.0 / 3.0) + ((phi9[5] - phi9[7]) + (phi9[8] - phi9[6])) * T(1.0 / 12.0);
+  const T gy = (phi9[2] - phi9[4]) * T(1.0 / 3.0) + ((phi9[5] - phi9[7]) + (phi9[6] - phi9[8])) * T(1.0 / 12.0);
+  T mu, Dx, Dy, lam = T(0), nnx = T(0), nny = T(0);
+  if (MODEL == MODEL_AC) {
+    const T lap = ((phi9[1] + phi9[3]) + (phi9[2] + phi9[4])) * T(2.0 / 3.0) +
+                  ((phi9[5] + phi9[7]) + (phi9[6] + phi9[8])) * T(1.0 / 6.0) - phi * T(10.0 / 3.0);
+    // chemical potential, Eq. (5)
+    mu = P.beta4 * (phi - P.phiA) * (phi - P.phiB) * (phi - P.phibar) - P.kappa * lap;
+    // conservative AC flux, Eqs. (7)-(8); n = 0 where |grad phi|^2 <= 1e-30
+    lam = P.lam_coef * (P.phiA - phi) * (phi - P.phiB);
+    const T g2 = gx * gx + gy * gy;
+    const T inv = g2 > T(1e-30) ? T(1) / sqrt(g2) : T(0);
+    nnx = gx * inv;
+    nny = gy * inv;
+    Dx = gx - lam * nnx;
+    Dy = gy - lam * nny;
+  } else {
+    // CH: D = grad mu_phi (Eq. (6)), mu9 holds mu_phi at x + c_i
+    mu = mu9[0];
+    Dx = (mu9[1] - mu9[3]) * T(1.0 / 3.0) + ((mu9[5] - mu9[7]) + (mu9[8] - mu9[6])) * T(1.0 / 12.0);
+    Dy = (mu9[2] - mu9[4]) * T(1.0 / 3.0) + ((mu9[5] - mu9[7]) + (mu9[6] - mu9[8])) * T(1.0 / 12.0);
+  }
+  // density (Eq. (10)), its gradient, consistent flux (Eq. (15)), force
+  const T rho = P.drho * (phi - P.phiB) + P.rhoB;
+  const T rx = P.drho * gx, ry = P.drho * gy;
+  const T mcx = -P.mob_drho * Dx, mcy = -P.mob_drho * Dy;
+  const T Gs = P.gravity_mode == 0 ? T(1) : (P.gravity_mode == 1 ? rho : rho - P.rho_mean);
+  const T Fx = mu * gx + Gs * P.gx, Fy = mu * gy + Gs * P.gy;
+
+  // zeroth- and first-order sums of g
+  const T ga = (g[1] + g[3]) + (g[2] + g[4]);
+  const T gb = (g[5] + g[7]) + (g[6] + g[8]);
+  const T g13 = g[1] - g[3], g24 = g[2] - g[4];
+  const T gdx = (g[5] - g[7]) + (g[8] - g[6]);
+  const T gdy = (g[5] - g[7]) + (g[6] - g[8]);
+  T u, v;
+  if (MODE == MODE_INIT) {
+    u = u_in;
+    v = v_in;
+  } else {
+    // Eq. (22b): rho u = sum c_i g_i + F/2
+    const T irho = T(1) / rho;
+    u = ((g13 + gdx) + T(0.5) * Fx) * irho;
+    v = ((g24 + gdy) + T(0.5) * Fy) * irho;
+  }
+  const T um = u * mcx + v * mcy;   // u . m
+  const T cA = u * mcx - v * mcy;   // u m_x - v m_y
+  const T cB = u * mcy + v * mcx;   // u m_y + v m_x
+  const T phu = phi * u, phv = phi * v;
+  T d_phu = T(0), d_phv = T(0), d_um = T(0), d_A = T(0), d_B = T(0);
+  if (MODE == MODE_STEP || MODE == MODE_MACRO) {
+    d_phu = phu - h[0];
+    d_phv = phv - h[1];
+    d_um = um - h[2];
+    d_A = cA - h[3];
+    d_B = cB - h[4];
+  }
+  const T uu = u * u + v * v;
+  const T ugr = u * rx + v * ry;
+  const T uF = u * Fx + v * Fy;
+  T p;
+  if (MODE == MODE_INIT) {
+    p = p_in;
+  } else {
+    // Eq. (39), second way: s_0 = -w_0 (rho u.u + u.m)/(2 c_s^2) = -(2/3)(...)
+    const T s0 = T(-2.0 / 3.0) * (rho * uu + um);
+    p = T(0.6) * ((ga + gb) + (T(0.5) + P.H) * ugr + s0 + P.K * (T(2) * uF + d_um));
+  }
+
+  if (MODE == MODE_HIST || MODE == MODE_STEP) {
+    {
+      B.hist[idx] = phu;
+      B.hist[P.plane + idx] = phv;
+      B.hist[2 * P.plane + idx] = um;
+      B.hist[3 * P.plane + idx] = cA;
+      B.hist[4 * P.plane + idx] = cB;
+    }
+    if (B.phi_prev) B.phi_prev[idx] = phi;
+    if (MODE == MODE_HIST) return;
+  }
+
+  // viscous rate s_g^{7,8} = 1/(nu/c_s^2 + 1/2), nu from Eq. (11) or (12)
+  T s7 = P.sg[7], s8 = P.sg[8];
+  if (P.sg7_node | P.sg8_node) {
+    const T frac = (phi - P.phiB) * P.inv_dphi;
+    T snode;
+    if (!P.visc_inverse) {
+      const T muv = frac * (P.muA - P.muB) + P.muB;
+      snode = rho / (T(3) * muv + T(0.5) * rho);
+    } else {
+      const T inu = frac * (P.inuA - P.inuB) + P.inuB;
+      snode = inu / (T(3) + T(0.5) * inu);
+    }
+    if (P.sg7_node) s7 = snode;
+    if (P.sg8_node) s8 = snode;
+  }
+
+  // hydrodynamic moments m = M g (deviation form: g_0 without rho0)
+  const T m0 = g[0] + ga + gb;
+  const T m1 = T(-4) * g[0] - ga + T(2) * gb;
+
+  // equilibrium moments, Eq. (C.2), minus rho0 (1, -4, 4, 0, ...)
+  const T E1 = T(6) * p + T(3) * (rho * uu + um);
+  const T E2 = T(-9) * p - T(3) * (rho * uu + um);
+  const T E3 = rho * u, E5 = rho * v;
+  const T E7 = cA + rho * (u * u - v * v);
+  const T E8 = T(0.5) * cB + rho * u * v;
+  // forcing moments, Eq. (C.2)
+  const T Q0 = ugr;
+  const T Q1 = T(3) * d_um + T(6) * uF;
+  const T Q2 = -ugr - Q1;
+  const T Q7 = T(2.0 / 3.0) * (u * rx - v * ry) + T(2) * (u * Fx - v * Fy) + d_A;
+  const T Q8 = T(1.0 / 3.0) * (u * ry + v * rx) + (u * Fy + v * Fx) + T(0.5) * d_B;
+
+  if (MODE == MODE_MACRO) {
+    // strain-rate trace, Eq. (35): tr S = -s_2/(2 rho c_s^2)[tr sum cc(g - g^eq) + tr M_2F / 2]
+    const T trneq = ((m1 - E1) + T(4) * m0) * T(1.0 / 3.0);
+    const T trM2F = (Q1 + T(4) * Q0) * T(1.0 / 3.0);
+    const T trS = -s7 * T(1.5) / rho * (trneq + T(0.5) * trM2F);
+    T* M = B.macro;
+    const long long pl = P.plane;
+    M[MAC_PHI * pl + idx] = phi;
+    M[MAC_UX * pl + idx] = u;
+    M[MAC_UY * pl + idx] = v;
+    M[MAC_P * pl + idx] = p;
+    M[MAC_RHO * pl + idx] = rho;
+    M[MAC_MU * pl + idx] = mu;
+    M[MAC_MCX * pl + idx] = mcx;
+    M[MAC_MCY * pl + idx] = mcy;
+    M[MAC_TRS * pl + idx] = trS;
+    return;
+  }
+
+  // ---- phase-field collision, Eq. (17) with Eq. (C.4) (AC) / (C.3) (CH)
+  const T chi = (MODEL == MODEL_AC) ? phi : mu;
+  const T e1 = T(-4) * phi + T(2) * P.eta * chi;
+  const T e2 = T(4) * phi - T(3) * P.eta * chi;
+  T Xx = d_phu, Xy = d_phv;
+  if (MODEL == MODEL_AC) {
+    Xx += lam * nnx * T(1.0 / 3.0);
+    Xy += lam * nny * T(1.0 / 3.0);
+  }
+  T fs[9];
+  if (MODE == MODE_INIT) {
+    // f^eq = M^{-1} m^eq
+    const T a = phi * T(1.0 / 9.0) - e1 * T(1.0 / 36.0) - e2 * T(1.0 / 18.0);
+    const T b = phi * T(1.0 / 9.0) + e1 * T(1.0 / 18.0) + e2 * T(1.0 / 36.0);
+    const T X = phu * T(1.0 / 3.0), Y = phv * T(1.0 / 3.0);        // m3/6 - m4/6 with m4 = -m3
+    const T Xd = phu * T(1.0 / 12.0), Yd = phv * T(1.0 / 12.0);    // m3/6 + m4/12
+    fs[0] = (phi - e1 + e2) * T(1.0 / 9.0);
+    fs[1] = a + X; fs[3] = a - X; fs[2] = a + Y; fs[4] = a - Y;
+    fs[5] = b + Xd + Yd; fs[6] = b - Xd + Yd; fs[7] = b - Xd - Yd; fs[8] = b + Xd - Yd;
+  } else {
+    const T fa = (f[1] + f[3]) + (f[2] + f[4]);
+    const T fb = (f[5] + f[7]) + (f[6] + f[8]);
+    const T f13 = f[1] - f[3], f24 = f[2] - f[4];
+    const T fdx = (f[5] - f[7]) + (f[8] - f[6]);
+    const T fdy = (f[5] - f[7]) + (f[6] - f[8]);
+    T m[9];
+    m[0] = f[0] + fa + fb;
+    m[1] = T(-4) * f[0] - fa + T(2) * fb;
+    m[2] = T(4) * f[0] - T(2) * fa + fb;
+    m[3] = f13 + fdx;
+    m[4] = T(-2) * f13 + fdx;
+    m[5] = f24 + fdy;
+    m[6] = T(-2) * f24 + fdy;
+    m[7] = (f[1] + f[3]) - (f[2] + f[4]);
+    m[8] = (f[5] + f[7]) - (f[6] + f[8]);
+    const T eq[9] = {phi, e1, e2, phu, -phu, phv, -phv, T(0), T(0)};
+    const T src[9] = {T(0), T(0), T(0), Xx, -Xx, Xy, -Xy, T(0), T(0)};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[k] = m[k] + P.sf[k] * (eq[k] - m[k]) + P.hf[k] * src[k];
+    const T a = m[0] * T(1.0 / 9.0) - m[1] * T(1.0 / 36.0) - m[2] * T(1.0 / 18.0);
+    const T b = m[0] * T(1.0 / 9.0) + m[1] * T(1.0 / 18.0) + m[2] * T(1.0 / 36.0);
+    const T X = (m[3] - m[4]) * T(1.0 / 6.0), Y = (m[5] - m[6]) * T(1.0 / 6.0);
+    const T Xd = m[3] * T(1.0 / 6.0) + m[4] * T(1.0 / 12.0);
+    const T Yd = m[5] * T(1.0 / 6.0) + m[6] * T(1.0 / 12.0);
+    const T Pp = m[7] * T(0.25), Qq = m[8] * T(0.25);
+    fs[0] = (m[0] - m[1] + m[2]) * T(1.0 / 9.0);
+    fs[1] = a + X + Pp; fs[3] = a - X + Pp; fs[2] = a + Y - Pp; fs[4] = a - Y - Pp;
+    fs[5] = b + Xd + Yd + Qq; fs[6] = b - Xd + Yd - Qq;
+    fs[7] = b - Xd - Yd + Qq; fs[8] = b + Xd - Yd - Qq;
+  }
+
+  // ---- hydrodynamic collision, Eq. (40) with Eq. (C.2)
+  T gs[9];
+  {
+    T m[9], eq[9], src[9];
+    if (MODE == MODE_INIT) {
+      m[0] = m[1] = m[2] = m[3] = m[4] = m[5] = m[6] = m[7] = m[8] = T(0);
+    } else {
+      m[0] = m0;
+      m[1] = m1;
+      m[2] = T(4) * g[0] - T(2) * ga + gb;
+      m[3] = g13 + gdx;
+      m[4] = T(-2) * g13 + gdx;
+      m[5] = g24 + gdy;
+      m[6] = T(-2) * g24 + gdy;
+      m[7] = (g[1] + g[3]) - (g[2] + g[4]);
+      m[8] = (g[5] + g[7]) - (g[6] + g[8]);
+    }
+    eq[0] = T(0); eq[1] = E1; eq[2] = E2; eq[3] = E3; eq[4] = -E3; eq[5] = E5; eq[6] = -E5;
+    eq[7] = E7; eq[8] = E8;
+    src[0] = Q0; src[1] = Q1; src[2] = Q2; src[3] = Fx; src[4] = -Fx; src[5] = Fy; src[6] = -Fy;
+    src[7] = Q7; src[8] = Q8;
+    if (MODE == MODE_INIT) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) m[k] = eq[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) m[k] = m[k] + P.sg[k] * (eq[k] - m[k]) + P.hg[k] * src[k];
+      m[7] = m[7] + s7 * (eq[7] - m[7]) + (T(1) - T(0.5) * s7) * src[7];
+      m[8] = m[8] + s8 * (eq[8] - m[8]) + (T(1) - T(0.5) * s8) * src[8];
+    }
+    const T a = m[0] * T(1.0 / 9.0) - m[1] * T(1.0 / 36.0) - m[2] * T(1.0 / 18.0);
+    const T b = m[0] * T(1.0 / 9.0) + m[1] * T(1.0 / 18.0) + m[2] * T(1.0 / 36.0);
+    const T X = (m[3] - m[4]) * T(1.0 / 6.0), Y = (m[5] - m[6]) * T(1.0 / 6.0);
+    const T Xd = m[3] * T(1.0 / 6.0) + m[4] * T(1.0 / 12.0);
+    const T Yd = m[5] * T(1.0 / 6.0) + m[6] * T(1.0 / 12.0);
+    const T Pp = m[7] * T(0.25), Qq = m[8] * T(0.25);
+    gs[0] = (m[0] - m[1] + m[2]) * T(1.0 / 9.0);
+    gs[1] = a + X + Pp; gs[3] = a - X + Pp; gs[2] = a + Y - Pp; gs[4] = a - Y - Pp;
+    gs[5] = b + Xd + Yd + Qq; gs[6] = b - Xd + Yd - Qq;
+    gs[7] = b - Xd - Yd + Qq; gs[8] = b + Xd - Yd - Qq;
+  }
+
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    B.fout[i * P.plane + idx] = fs[i];
+    B.gout[i * P.plane + idx] = gs[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The fused marching kernel.
+// ---------------------------------------------------------------------------
+template <typename T, int MODEL, int MODE>
+__global__ void __launch_bounds__(BX) k_march(const Phys<T> P, const Bufs<T> B) {
+  constexpr int R = (MODEL == MODEL_CH) ? 2 : 1;  // phi halo radius
+  constexpr int WS = BX + 2 * R;                  // phi ring row width
+  __shared__ T sphi[RING][WS];
+  __shared__ T smu[(MODEL == MODEL_CH) ? RING : 1][BX + 2];
+
+  const int tid = threadIdx.x;
+  const int nx = P.nx, ny = P.ny;
+  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * LY;
+  const int w = min(BX, nx - x0);
+  const int y1 = min(y0 + LY, ny);
+  const bool active = tid < w;
+  const int x = x0 + tid;
+  const bool left_edge = (x0 == 0), right_edge = (x0 + w == nx);
+  const bool halo_l = (tid == 0), halo_r = (tid == w - 1);
+
+  // Pulled populations of the rows not yet processed (look-ahead queue).
+  T fq[R + 1][9];
+
+  // -- make phi of row r (in-domain or periodic wrap) into the ring: own
+  //    column, and the halo columns (threads 0 and w-1).  x-wall ghosts are
+  //    computed by the halo threads from their own values (no barrier).
+  auto make_row = [&](int r, int q) {
+    int rr = r;
+    if (rr < 0) rr += ny;
+    if (rr >= ny) rr -= ny;
+    const int s = slot_of(r);
+    if (active) {
+      T v;
+      if (MODE == MODE_INIT) {
+        v = T(B.iphi[(long long)rr * nx + x]);
+      } else {
+        pull9(B.fin, P, x, rr, fq[q]);
+        v = sum9(fq[q]);
+      }
+      sphi[s][tid + R] = v;
+      if (halo_l) {
+#pragma unroll
+        for (int k = 1; k <= R; ++k) {
+          int xh = x0 - k;
+          T hv;
+          if (xh >= 0) {
+            hv = phi_at<T, MODE>(P, B, xh, rr);
+          } else if (!P.wall_x) {
+            hv = phi_at<T, MODE>(P, B, xh + nx, rr);
+          } else {
+            hv = wall_ghost(P, SIDE_LEFT, v, phi_at<T, MODE>(P, B, 1, rr));
+          }
+          sphi[s][R - k] = hv;
+        }
+      }
+      if (halo_r) {
+#pragma unroll
+        for (int k = 1; k <= R; ++k) {
+          int xh = x0 + w - 1 + k;
+          T hv;
+          if (xh < nx) {
+            hv = phi_at<T, MODE>(P, B, xh, rr);
+          } else if (!P.wall_x) {
+            hv = phi_at<T, MODE>(P, B, xh - nx, rr);
+          } else {
+            hv = wall_ghost(P, SIDE_RIGHT, v, phi_at<T, MODE>(P, B, nx - 2, rr));
+          }
+          sphi[s][w - 1 + R + k] = hv;
+        }
+      }
+    }
+  };
+  // -- y-wall ghost row from two in-domain rows (after a barrier)
+  auto ghost_row = [&](int r_ghost, int r1, int r2, int side) {
+    const int sg = slot_of(r_ghost), s1 = slot_of(r1), s2 = slot_of(r2);
+    for (int j = tid; j < w + 2 * R; j += BX) sphi[sg][j] = wall_ghost(P, side, sphi[s1][j], sphi[s2][j]);
+  };
+  // -- CH: mu_phi of row r over columns [-1, w] into the mu ring
+  auto make_mu = [&](int r) {
+    if (MODEL != MODEL_CH) return;
+    const int s = slot_of(r);
+    const int sm = slot_of(r - 1), sp = slot_of(r + 1);
+    for (int j = tid - 1; j <= w; j += BX) {
+      const int c = j + R;
+      const T ph = sphi[s][c];
+      const T lap = ((sphi[s][c + 1] + sphi[s][c - 1]) + (sphi[sp][c] + sphi[sm][c])) * T(2.0 / 3.0) +
+                    ((sphi[sp][c + 1] + sphi[sm][c - 1]) + (sphi[sp][c - 1] + sphi[sm][c + 1])) * T(1.0 / 6.0) -
+                    ph * T(10.0 / 3.0);
+      smu[s][j + 1] = P.beta4 * (ph - P.phiA) * (ph - P.phiB) * (ph - P.phibar) - P.kappa * lap;
+    }
+  };
+  // -- CH: mirror ghosts of mu (x walls after make_mu, y walls whole rows)
+  auto mu_xmirror = [&](int r) {
+    if (MODEL != MODEL_CH || !P.wall_x) return;
+    const int s = slot_of(r);
+    if (left_edge && tid == 0) smu[s][0] = smu[s][1];
+    if (right_edge && tid == 0) smu[s][w + 1] = smu[s][w];
+  };
+  auto mu_row_copy = [&](int r_dst, int r_src) {
+    const int sd = slot_of(r_dst), ss = slot_of(r_src);
+    for (int j = tid; j < w + 2; j += BX) smu[sd][j] = smu[ss][j];
+  };
+
+  const bool wy = P.wall_y != 0;
+
+  // ------------------------------------------------------------ prologue
+  // AC: rows y0-1, y0 (keep f of y0).  CH: rows y0-2 .. y0+1 (keep y0, y0+1).
+#pragma unroll
+  for (int k = -R; k <= R - 1; ++k) {
+    const int r = y0 + k;
+    const bool in = (r >= 0 && r < ny);
+    if (in || !wy) make_row(r, k >= 0 ? k : 0);
+  }
+  __syncthreads();
+  if (R == 2 && wy) {
+    // CH look-ahead reaches a wall inside the prologue: the bottom ghost
+    // needs rows 0 and 1, the top ghost (segment starting at ny-1) rows
+    // ny-1 and ny-2 -- all made above.  (AC makes these ghosts in the march.)
+    if (y0 == 0) {
+      ghost_row(-1, 0, 1, SIDE_BOTTOM);
+      __syncthreads();
+    }
+    if (y0 + R - 1 >= ny) {
+      ghost_row(ny, ny - 1, ny - 2, SIDE_TOP);
+      __syncthreads();
+    }
+  }
+  if (MODEL == MODEL_CH) {
+    // mu of rows y0-1 and y0
+    if (wy && y0 == 0) {
+      make_mu(0);
+      __syncthreads();
+      mu_xmirror(0);
+      __syncthreads();
+      mu_row_copy(-1, 0);
+    } else {
+      make_mu(y0 - 1);
+      make_mu(y0);
+      __syncthreads();
+      mu_xmirror(y0 - 1);
+      mu_xmirror(y0);
+    }
+    __syncthreads();
+  }
+
+  // ------------------------------------------------------------ march
+  for (int y = y0; y < y1; ++y) {
+    // make the look-ahead phi row y + R
+    const int rn = y + R;
+    const bool rn_in = rn < ny;
+    if (rn_in || !wy) make_row(rn, R);
+    // loads of the current row's g and history
+    T g[9] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+    T h[5] = {T(0), T(0), T(0), T(0), T(0)};
+    T uin = T(0), vin = T(0), pin = T(0);
+    const long long idx = (long long)y * P.pitch + x;
+    if (active) {
+      if (MODE == MODE_INIT) {
+        const long long di = (long long)y * nx + x;
+        if (B.iux) uin = T(B.iux[di]);
+        if (B.iuy) vin = T(B.iuy[di]);
+        if (B.ip) pin = T(B.ip[di]);
+      } else {
+        pull9(B.gin, P, x, y, g);
+        if (MODE == MODE_STEP || MODE == MODE_MACRO) {
+#pragma unroll
+          for (int k = 0; k < 5; ++k) h[k] = B.hist[k * P.plane + idx];
+        }
+      }
+    }
+    __syncthreads();
+    if (wy) {
+      if (R == 1 && y == 0) {  // bottom ghost now that row 1 exists
+        ghost_row(-1, 0, 1, SIDE_BOTTOM);
+        __syncthreads();
+      }
+      if (rn == ny) {  // top ghost from rows ny-1, ny-2
+        ghost_row(ny, ny - 1, ny - 2, SIDE_TOP);
+        __syncthreads();
+      }
+    }
+    if (MODEL == MODEL_CH) {
+      const int rm = y + 1;  // mu row needed next
+      if (rm < ny || !wy) {
+        make_mu(rm);
+        __syncthreads();
+        mu_xmirror(rm);
+      } else if (rm == ny) {
+        mu_row_copy(ny, ny - 1);
+      }
+      __syncthreads();
+    }
+
+    if (active) {
+      const int sm = slot_of(y - 1), s0 = slot_of(y), sp = slot_of(y + 1);
+      const int c = tid + R;
+      T phi9[9];
+      phi9[0] = sphi[s0][c];
+      phi9[1] = sphi[s0][c + 1];
+      phi9[2] = sphi[sp][c];
+      phi9[3] = sphi[s0][c - 1];
+      phi9[4] = sphi[sm][c];
+      phi9[5] = sphi[sp][c + 1];
+      phi9[6] = sphi[sp][c - 1];
+      phi9[7] = sphi[sm][c - 1];
+      phi9[8] = sphi[sm][c + 1];
+      T mu9[9];
+      if (MODEL == MODEL_CH) {
+        const int cm = tid + 1;
+        mu9[0] = smu[s0][cm];
+        mu9[1] = smu[s0][cm + 1];
+        mu9[2] = smu[sp][cm];
+        mu9[3] = smu[s0][cm - 1];
+        mu9[4] = smu[sm][cm];
+        mu9[5] = smu[sp][cm + 1];
+        mu9[6] = smu[sp][cm - 1];
+        mu9[7] = smu[sm][cm - 1];
+        mu9[8] = smu[sm][cm + 1];
+      }
+      node_update<T, MODEL, MODE>(P, B, idx, phi9, mu9, fq[0], g, h, uin, vin, pin);
+    }
+    // advance the queue of pulled f
+#pragma unroll
+    for (int q = 0; q < R; ++q)
+#pragma unroll
+      for (int i = 0; i < 9; ++i) fq[q][i] = fq[q + 1][i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Auxiliary kernels: gather the pulled populations, scatter populations back
+// into the pre-stream layout, convert planes, diagnostics reductions.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_pull(const Phys<T> P, const T* __restrict__ in, T* __restrict__ out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= P.nx) return;
+  T v[9];
+  pull9(in, P, x, y, v);
+  const long long idx = (long long)y * P.pitch + x;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) out[i * P.plane + idx] = v[i];
+}
+
+// Inverse of the pull: the population node x sees in direction i came from
+// x - c_i (or, beyond a wall, from x itself in direction opp(i)).  Every
+// destination entry is written exactly once.
+template <typename T>
+__global__ void k_unstream(const Phys<T> P, const T* __restrict__ in, T* __restrict__ out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= P.nx) return;
+  const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  const int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  const int op[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+  const long long idx = (long long)y * P.pitch + x;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    int sx = x - cx[i], sy = y - cy[i];
+    bool wall = false;
+    if (sx < 0 || sx >= P.nx) { if (P.wall_x) wall = true; else sx = (sx + P.nx) % P.nx; }
+    if (sy < 0 || sy >= P.ny) { if (P.wall_y) wall = true; else sy = (sy + P.ny) % P.ny; }
+    const T val = in[i * P.plane + idx];
+    if (wall) out[op[i] * P.plane + idx] = val;
+    else out[i * P.plane + (long long)sy * P.pitch + sx] = val;
+  }
+}
+
+// pitched T planes -> dense double planes of the region [x0, x0+w) x
+// [y0, y0+hgt) (plane 0 gets + add0)
+template <typename T>
+__global__ void k_export(const Phys<T> P, const T* __restrict__ in, double* __restrict__ out,
+                         int planes, double add0, int x0, int y0, int w, int hgt) {
+  const int xx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int yy = blockIdx.y;
+  if (xx >= w) return;
+  const long long src = (long long)(y0 + yy) * P.pitch + (x0 + xx);
+  for (int k = 0; k < planes; ++k)
+    out[(long long)k * w * hgt + (long long)yy * w + xx] =
+        double(in[k * P.plane + src]) + (k == 0 ? add0 : 0.0);
+}
+
+template <typename T>
+__global__ void k_import(const Phys<T> P, const double* __restrict__ in, T* __restrict__ out,
+                         int planes, double sub0) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= P.nx) return;
+  for (int k = 0; k < planes; ++k)
+    out[k * P.plane + (long long)y * P.pitch + x] =
+        T(in[(long long)k * P.nx * P.ny + (long long)y * P.nx + x] - (k == 0 ? sub0 : 0.0));
+}
+
+// Diagnostics, Eqs. (42)-(43), from the MACRO planes and phi(t-1).
+// Per block: [sum phi, sum trS^2, sum S_m^2, max|u|, non-finite, count].
+constexpr int DIAG_THREADS = 256;
+constexpr int DIAG_FIELDS = 6;
+
+__device__ __forceinline__ void warp_reduce6(double v[DIAG_FIELDS]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < DIAG_FIELDS; ++k) {
+      const double other = __shfl_down_sync(0xffffffffu, v[k], o);
+      v[k] = (k == 3) ? fmax(v[k], other) : v[k] + other;
+    }
+  }
+}
+
+__device__ __forceinline__ void block_reduce6(double v[DIAG_FIELDS], double* out) {
+  __shared__ double red[DIAG_THREADS / 32][DIAG_FIELDS];
+  warp_reduce6(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < DIAG_FIELDS; ++k) red[wid][k] = v[k];
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < DIAG_FIELDS; ++k)
+      v[k] = lane < DIAG_THREADS / 32 ? red[lane][k] : 0.0;
+    warp_reduce6(v);
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < DIAG_FIELDS; ++k) out[k] = v[k];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(const Phys<T> P, const T* __restrict__ mac,
+                                                               const T* __restrict__ phi_prev,
+                                                               double* __restrict__ partial) {
+  double v[DIAG_FIELDS] = {0, 0, 0, 0, 0, 0};
+  const long long N = (long long)P.nx * P.ny;
+  const long long pl = P.plane;
+  const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  const int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  const double wi[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(n / P.nx), x = (int)(n - (long long)y * P.nx);
+    const long long id = (long long)y * P.pitch + x;
+    const double phi = double(mac[MAC_PHI * pl + id]);
+    const double u = double(mac[MAC_UX * pl + id]), vv = double(mac[MAC_UY * pl + id]);
+    const double um2 = u * u + vv * vv;
+    v[0] += phi;
+    if (!isfinite(phi) || !isfinite(um2)) {
+      v[4] += 1.0;
+    } else {
+      v[3] = fmax(v[3], sqrt(um2));
+    }
+    if ((P.wall_x && (x == 0 || x == P.nx - 1)) || (P.wall_y && (y == 0 || y == P.ny - 1))) continue;
+    const double trS = double(mac[MAC_TRS * pl + id]);
+    double div = 0.0;
+#pragma unroll
+    for (int k = 1; k < 9; ++k) {
+      int xn = x + cx[k], yn = y + cy[k];
+      xn = xn < 0 ? xn + P.nx : (xn >= P.nx ? xn - P.nx : xn);
+      yn = yn < 0 ? yn + P.ny : (yn >= P.ny ? yn - P.ny : yn);
+      const long long q = (long long)yn * P.pitch + xn;
+      const double rq = double(mac[MAC_RHO * pl + q]);
+      const double Jx = rq * double(mac[MAC_UX * pl + q]) + double(mac[MAC_MCX * pl + q]);
+      const double Jy = rq * double(mac[MAC_UY * pl + q]) + double(mac[MAC_MCY * pl + q]);
+      div += wi[k] * (cx[k] * Jx + cy[k] * Jy) * 3.0;
+    }
+    const double sm = double(P.drho) * (phi - double(phi_prev[id])) + div;
+    v[1] += trS * trS;
+    v[2] += sm * sm;
+    v[5] += 1.0;
+  }
+  block_reduce6(v, partial + (long long)blockIdx.x * DIAG_FIELDS);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(DIAG_THREADS) k_diag_final(const double* __restrict__ partial,
+                                                             int nparts, double* __restrict__ out) {
+  double v[DIAG_FIELDS] = {0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < DIAG_FIELDS; ++k)
+      v[k] = (k == 3) ? fmax(v[k], partial[b * DIAG_FIELDS + k]) : v[k] + partial[b * DIAG_FIELDS + k];
+  }
+  block_reduce6(v, out);
+}
+
+}  // namespace pflbm

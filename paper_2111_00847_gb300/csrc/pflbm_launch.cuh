@@ -1,0 +1,74 @@
+// Definitions of the launch wrappers declared in pflbm_launch.h.
+#pragma once
+
+#include "pflbm_launch.h"
+
+namespace pflbm {
+
+template <typename T, int MODEL>
+static cudaError_t launch_march_model(int mode, const Phys<T>& P, const Bufs<T>& B, cudaStream_t s) {
+  const dim3 grid((P.nx + BX - 1) / BX, (P.ny + LY - 1) / LY);
+  switch (mode) {
+    case MODE_STEP: k_march<T, MODEL, MODE_STEP><<<grid, BX, 0, s>>>(P, B); break;
+    case MODE_MACRO: k_march<T, MODEL, MODE_MACRO><<<grid, BX, 0, s>>>(P, B); break;
+    case MODE_HIST: k_march<T, MODEL, MODE_HIST><<<grid, BX, 0, s>>>(P, B); break;
+    case MODE_INIT: k_march<T, MODEL, MODE_INIT><<<grid, BX, 0, s>>>(P, B); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_march(int model, int mode, const Phys<T>& P, const Bufs<T>& B, cudaStream_t s) {
+  return model == MODEL_CH ? launch_march_model<T, MODEL_CH>(mode, P, B, s)
+                           : launch_march_model<T, MODEL_AC>(mode, P, B, s);
+}
+
+static inline dim3 row_grid(int nx, int ny, int threads) { return dim3((nx + threads - 1) / threads, ny); }
+
+template <typename T>
+cudaError_t launch_pull(const Phys<T>& P, const T* in, T* out, cudaStream_t s) {
+  k_pull<T><<<row_grid(P.nx, P.ny, 128), 128, 0, s>>>(P, in, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_unstream(const Phys<T>& P, const T* in, T* out, cudaStream_t s) {
+  k_unstream<T><<<row_grid(P.nx, P.ny, 128), 128, 0, s>>>(P, in, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_export(const Phys<T>& P, const T* in, double* out, int planes, double add0,
+                          int x0, int y0, int w, int hgt, cudaStream_t s) {
+  k_export<T><<<row_grid(w, hgt, 128), 128, 0, s>>>(P, in, out, planes, add0, x0, y0, w, hgt);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_import(const Phys<T>& P, const double* in, T* out, int planes, double sub0,
+                          cudaStream_t s) {
+  k_import<T><<<row_grid(P.nx, P.ny, 128), 128, 0, s>>>(P, in, out, planes, sub0);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_diag(const Phys<T>& P, const T* macro, const T* phi_prev, double* partial,
+                        int nparts, double* out, cudaStream_t s) {
+  k_diag_partial<T><<<nparts, DIAG_THREADS, 0, s>>>(P, macro, phi_prev, partial);
+  k_diag_final<T><<<1, DIAG_THREADS, 0, s>>>(partial, nparts, out);
+  return cudaGetLastError();
+}
+
+#define PFLBM_INSTANTIATE(T)                                                                        \
+  template cudaError_t launch_march<T>(int, int, const Phys<T>&, const Bufs<T>&, cudaStream_t);   \
+  template cudaError_t launch_pull<T>(const Phys<T>&, const T*, T*, cudaStream_t);                \
+  template cudaError_t launch_unstream<T>(const Phys<T>&, const T*, T*, cudaStream_t);            \
+  template cudaError_t launch_export<T>(const Phys<T>&, const T*, double*, int, double, int, int,  \
+                                        int, int, cudaStream_t);                                   \
+  template cudaError_t launch_import<T>(const Phys<T>&, const double*, T*, int, double,           \
+                                        cudaStream_t);                                             \
+  template cudaError_t launch_diag<T>(const Phys<T>&, const T*, const T*, double*, int, double*,  \
+                                      cudaStream_t);
+
+}  // namespace pflbm

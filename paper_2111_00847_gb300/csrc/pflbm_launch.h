@@ -1,0 +1,28 @@
+// Host-side launch wrappers of the device kernels (defined in
+// pflbm_launch.cuh, instantiated for float and double in pflbm_f32.cu and
+// pflbm_f64.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pflbm_kernels.cuh"
+
+namespace pflbm {
+
+template <typename T>
+cudaError_t launch_march(int model, int mode, const Phys<T>& P, const Bufs<T>& B, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pull(const Phys<T>& P, const T* in, T* out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_unstream(const Phys<T>& P, const T* in, T* out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_export(const Phys<T>& P, const T* in, double* out, int planes, double add0,
+                          int x0, int y0, int w, int hgt, cudaStream_t s);
+template <typename T>
+cudaError_t launch_import(const Phys<T>& P, const double* in, T* out, int planes, double sub0,
+                          cudaStream_t s);
+template <typename T>
+cudaError_t launch_diag(const Phys<T>& P, const T* macro, const T* phi_prev, double* partial,
+                        int nparts, double* out, cudaStream_t s);
+
+}  // namespace pflbm
