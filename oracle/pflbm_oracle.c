@@ -124,7 +124,7 @@ typedef struct {
     long N;
     long t;
     /* free-energy constants, Eq. (3), and density slope, Eq. (10) */
-    double beta, kappa, dphi, drho_dphi, lam_coef;
+    double beta, kappa, dphi, drho_dphi, lam_coef, n_delta;
     /* rates: constant value, or NaN for the per-node default rule */
     double sf[9], sg[9];
     double Hc, Kc;            /* pressure-scheme constants, App. C */
@@ -351,19 +351,21 @@ static void phase_pass(ostate *st)
         for (long n = 0; n < N; ++n) st->lam[n] = st->nxv[n] = st->nyv[n] = 0.0;
     } else {
         /* AC: lambda = sqrt(2 beta/k)(phiA - phi)(phi - phiB) = 4 (phiA-phi)(phi-phiB)/(W dphi),
-         * n = grad phi / |grad phi| (taken as 0 where |grad phi|^2 <= 1e-30),
-         * D = grad phi - lambda n  (Eqs. (7)-(8)) */
+         * n = grad phi / |grad phi|, D = grad phi - lambda n  (Eqs. (7)-(8)).
+         * n is undefined where grad phi = 0; reading: n = grad phi / max(|grad phi|, delta_n)
+         * with delta_n = 1e-3 dphi / W, a thousandth of the gradient scale of the interface.
+         * It equals the unit normal wherever |grad phi| >= delta_n (the whole interface
+         * except its far tails) and makes lambda n a Lipschitz function of grad phi in the
+         * bulk, where an overshoot phi > phiA (or < phiB) makes lambda nonzero and the
+         * direction of a round-off-level gradient would otherwise enter the scheme. */
 #pragma omp parallel for schedule(static)
         for (long n = 0; n < N; ++n) {
             const double ph = st->phi[n];
             const double lam = st->lam_coef * (phiA - ph) * (ph - phiB);
-            const double g2 = st->gpx[n] * st->gpx[n] + st->gpy[n] * st->gpy[n];
-            double nxn = 0.0, nyn = 0.0;
-            if (g2 > 1e-30) {
-                const double gm = sqrt(g2);
-                nxn = st->gpx[n] / gm;
-                nyn = st->gpy[n] / gm;
-            }
+            const double gnorm = sqrt(st->gpx[n] * st->gpx[n] + st->gpy[n] * st->gpy[n]);
+            const double gm = gnorm > st->n_delta ? gnorm : st->n_delta;
+            const double nxn = st->gpx[n] / gm;
+            const double nyn = st->gpy[n] / gm;
             st->lam[n] = lam;
             st->nxv[n] = nxn;
             st->nyv[n] = nyn;
@@ -716,6 +718,7 @@ int oracle_create(const oracle_params *P, ostate **out)
      * and given that value when sigma = 0 switches surface tension off */
     st->lam_coef = P->sigma > 0.0 ? sqrt(2.0 * st->beta / st->kappa) : 4.0 / (P->width * st->dphi);
     st->drho_dphi = (P->rhoA - P->rhoB) / st->dphi;
+    st->n_delta = 1e-3 * st->dphi / P->width;
     for (int k = 0; k < 9; ++k) { st->sf[k] = P->s_f[k]; st->sg[k] = P->s_g[k]; }
     /* App. C (first matrix): H = (s_g^2 - s_g^0)/(9 s_g^0 s_g^2), K = 1/(3c^2) */
     {

@@ -61,6 +61,7 @@ struct Phys {
   int gravity_mode, visc_inverse, sg7_node, sg8_node;
   T phiA, phiB, phibar, inv_dphi;
   T beta4, kappa, lam_coef;  // 4 beta, k, sqrt(2 beta / k)   (Eqs. (3), (5), (8))
+  T n_delta;                 // floor of |grad phi| in n = grad phi / |grad phi|
   T drho, rhoB, rho_mean;    // d rho / d phi, rho_B, (rho_A + rho_B)/2
   T mob_drho;                // (d rho/d phi) M_phi, zero for the original model
   T muA, muB, inuA, inuB;    // mu_A, mu_B, 1/nu_A, 1/nu_B
@@ -162,14 +163,17 @@ __device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, 
   const T gy = (phi9[2] - phi9[4]) * T(1.0 / 3.0) + ((phi9[5] - phi9[7]) + (phi9[6] - phi9[8])) * T(1.0 / 12.0);
   T mu, Dx, Dy, lam = T(0), nnx = T(0), nny = T(0);
   if (MODEL == MODEL_AC) {
-    const T lap = ((phi9[1] + phi9[3]) + (phi9[2] + phi9[4])) * T(2.0 / 3.0) +
-                  ((phi9[5] + phi9[7]) + (phi9[6] + phi9[8])) * T(1.0 / 6.0) - phi * T(10.0 / 3.0);
+    // differences first: neighbouring phi are close, so phi_i - phi is exact
+    const T lap = (((phi9[1] - phi) + (phi9[3] - phi)) + ((phi9[2] - phi) + (phi9[4] - phi))) * T(2.0 / 3.0) +
+                  (((phi9[5] - phi) + (phi9[7] - phi)) + ((phi9[6] - phi) + (phi9[8] - phi))) * T(1.0 / 6.0);
     // chemical potential, Eq. (5)
     mu = P.beta4 * (phi - P.phiA) * (phi - P.phiB) * (phi - P.phibar) - P.kappa * lap;
-    // conservative AC flux, Eqs. (7)-(8); n = 0 where |grad phi|^2 <= 1e-30
+    // conservative AC flux, Eqs. (7)-(8), n = grad phi / max(|grad phi|, delta_n)
+    // (delta_n = 1e-3 dphi / W: the unit normal across the interface, and a
+    // Lipschitz function of grad phi in the bulk where |grad phi| -> 0)
     lam = P.lam_coef * (P.phiA - phi) * (phi - P.phiB);
-    const T g2 = gx * gx + gy * gy;
-    const T inv = g2 > T(1e-30) ? T(1) / sqrt(g2) : T(0);
+    const T gnorm = sqrt(gx * gx + gy * gy);
+    const T inv = T(1) / (gnorm > P.n_delta ? gnorm : P.n_delta);
     nnx = gx * inv;
     nny = gy * inv;
     Dx = gx - lam * nnx;
@@ -440,8 +444,9 @@ __global__ void __launch_bounds__(BX) k_march(const Phys<T> P, const Bufs<T> B) 
             hv = phi_at<T, MODE>(P, B, xh, rr);
           } else if (!P.wall_x) {
             hv = phi_at<T, MODE>(P, B, xh + nx, rr);
-          } else {
-            hv = wall_ghost(P, SIDE_LEFT, v, phi_at<T, MODE>(P, B, 1, rr));
+          } else {  // ghost beyond the left wall, from columns 0 and 1
+            const T p1 = (x == 0) ? v : phi_at<T, MODE>(P, B, 0, rr);
+            hv = wall_ghost(P, SIDE_LEFT, p1, phi_at<T, MODE>(P, B, 1, rr));
           }
           sphi[s][R - k] = hv;
         }
@@ -455,8 +460,9 @@ __global__ void __launch_bounds__(BX) k_march(const Phys<T> P, const Bufs<T> B) 
             hv = phi_at<T, MODE>(P, B, xh, rr);
           } else if (!P.wall_x) {
             hv = phi_at<T, MODE>(P, B, xh - nx, rr);
-          } else {
-            hv = wall_ghost(P, SIDE_RIGHT, v, phi_at<T, MODE>(P, B, nx - 2, rr));
+          } else {  // ghost beyond the right wall, from columns nx-1 and nx-2
+            const T p1 = (x == nx - 1) ? v : phi_at<T, MODE>(P, B, nx - 1, rr);
+            hv = wall_ghost(P, SIDE_RIGHT, p1, phi_at<T, MODE>(P, B, nx - 2, rr));
           }
           sphi[s][w - 1 + R + k] = hv;
         }
@@ -476,9 +482,10 @@ __global__ void __launch_bounds__(BX) k_march(const Phys<T> P, const Bufs<T> B) 
     for (int j = tid - 1; j <= w; j += BX) {
       const int c = j + R;
       const T ph = sphi[s][c];
-      const T lap = ((sphi[s][c + 1] + sphi[s][c - 1]) + (sphi[sp][c] + sphi[sm][c])) * T(2.0 / 3.0) +
-                    ((sphi[sp][c + 1] + sphi[sm][c - 1]) + (sphi[sp][c - 1] + sphi[sm][c + 1])) * T(1.0 / 6.0) -
-                    ph * T(10.0 / 3.0);
+      const T lap = (((sphi[s][c + 1] - ph) + (sphi[s][c - 1] - ph)) + ((sphi[sp][c] - ph) + (sphi[sm][c] - ph))) *
+                        T(2.0 / 3.0) +
+                    (((sphi[sp][c + 1] - ph) + (sphi[sm][c - 1] - ph)) + ((sphi[sp][c - 1] - ph) + (sphi[sm][c + 1] - ph))) *
+                        T(1.0 / 6.0);
       smu[s][j + 1] = P.beta4 * (ph - P.phiA) * (ph - P.phiB) * (ph - P.phibar) - P.kappa * lap;
     }
   };
