@@ -71,6 +71,8 @@ enum { LBM_G_CONST = 0, LBM_G_RHO = 1, LBM_G_RHO_MINUS_MEAN = 2 };
 /* lbm_params.bc[side] */
 enum { LBM_PERIODIC = 0, LBM_WALL = 1 };
 enum { LBM_LEFT = 0, LBM_RIGHT = 1, LBM_BOTTOM = 2, LBM_TOP = 3 };
+/* lbm_params.flags */
+enum { LBM_FLAG_NO_TMA = 1 };
 /* lbm_fields / lbm_set_fields selector */
 enum {
     LBM_PHI = 0,   /* order parameter phi = sum_i f_i          [ny][nx]    */
@@ -107,12 +109,15 @@ enum {
  *  diag_every   if > 0, lbm_step computes the diagnostics every diag_every
  *               steps (and then synchronises) and fails with LBM_EUNSTABLE
  *               on a non-finite value or |u| > 0.4
+ *  flags        LBM_FLAG_NO_TMA: step with the register-pipelined kernel
+ *               instead of the TMA-staged one (same arithmetic, for A/B
+ *               comparison); 0 otherwise
  */
 typedef struct lbm_params {
     int32_t version, nx, ny, precision;
     int32_t phase_model, flux_model, visc_law, gravity_mode;
     int32_t bc[4];
-    int32_t diag_every, reserved;
+    int32_t diag_every, flags;
     double phiA, phiB, rhoA, rhoB, muA, muB;
     double mobility, width, sigma, eta;
     double gx, gy, rho0;

@@ -28,6 +28,7 @@ LBM_FP64, LBM_FP32, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2, 3
  LBM_MCX, LBM_MCY) = range(12)
 LBM_NDIAG = 8
 LBM_ABI_VERSION = 1
+LBM_FLAG_NO_TMA = 1
 DIAG_KEYS = ("t", "sum_phi", "Du_rms", "Sm_rms", "umax", "nonfinite", "n_avg", "reserved")
 
 EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_fields", "lbm_fields_region",
@@ -42,7 +43,7 @@ class LbmParams(C.Structure):
         ("version", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("precision", C.c_int32),
         ("phase_model", C.c_int32), ("flux_model", C.c_int32), ("visc_law", C.c_int32),
         ("gravity_mode", C.c_int32), ("bc", C.c_int32 * 4), ("diag_every", C.c_int32),
-        ("reserved", C.c_int32),
+        ("flags", C.c_int32),
         ("phiA", C.c_double), ("phiB", C.c_double), ("rhoA", C.c_double), ("rhoB", C.c_double),
         ("muA", C.c_double), ("muB", C.c_double), ("mobility", C.c_double), ("width", C.c_double),
         ("sigma", C.c_double), ("eta", C.c_double), ("gx", C.c_double), ("gy", C.c_double),
@@ -102,6 +103,7 @@ def params_struct(prm) -> LbmParams:
     for name in ("nx", "ny", "precision", "phase_model", "flux_model", "visc_law",
                  "gravity_mode", "diag_every"):
         setattr(s, name, int(getattr(prm, name)))
+    s.flags = int(getattr(prm, "flags", 0))
     for i in range(4):
         s.bc[i] = int(prm.bc[i])
         s.theta_deg[i] = float(prm.theta_deg[i])

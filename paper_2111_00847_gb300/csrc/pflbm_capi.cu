@@ -34,6 +34,8 @@ struct lbm_handle {
   int dstage_planes = 0;
   double* dpart = nullptr;
   double* ddiag = nullptr;
+  int* derr = nullptr;  // device flag raised by a kernel whose bounded wait timed out
+  bool use_tma = true;
   int nparts = 0;
   double diag[LBM_NDIAG] = {0};
   int64_t t = 0;
@@ -101,7 +103,7 @@ static int validate(const lbm_params* P) {
   if (!P) return fail(nullptr, LBM_EINVAL, "params is NULL");
   if (P->version != LBM_ABI_VERSION) return fail(nullptr, LBM_EINVAL, "params.version %d != %d", P->version, LBM_ABI_VERSION);
   if (P->nx < 3 || P->ny < 3) return fail(nullptr, LBM_EINVAL, "grid %d x %d: each side must be >= 3", P->nx, P->ny);
-  const long long pitch = ((long long)P->nx + 31) / 32 * 32;
+  const long long pitch = ((long long)P->nx + 2 * XPAD + 4 + 31) / 32 * 32;
   if (P->ny > 65535) return fail(nullptr, LBM_EINVAL, "ny = %d exceeds 65535", P->ny);
   if (pitch * P->ny >= (1LL << 31)) return fail(nullptr, LBM_EINVAL, "grid %d x %d too large (pitch*ny must be < 2^31)", P->nx, P->ny);
   if (P->precision == LBM_FP16_DEV || P->precision == LBM_BF16_DEV)
@@ -127,6 +129,7 @@ static int validate(const lbm_params* P) {
   const double amax = 4.0 / (P->width * (P->phiA - P->phiB));
   if (8.0 / 3.0 - amax * std::fabs(P->phiA + P->phiB) <= 0.0) return fail(nullptr, LBM_EINVAL, "interface width too small for the wetting root");
   if (P->diag_every < 0) return fail(nullptr, LBM_EINVAL, "diag_every < 0");
+  if (P->flags & ~LBM_FLAG_NO_TMA) return fail(nullptr, LBM_EINVAL, "unknown flags 0x%x", P->flags);
   return LBM_OK;
 }
 
@@ -227,6 +230,19 @@ static int ensure_macro(lbm_handle* h) {
   return LBM_OK;
 }
 
+// A kernel whose bounded wait timed out raised *derr; report it once the
+// stream has been synchronised.
+static int check_device_flag(lbm_handle* h) {
+  int flag = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(&flag, h->derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (flag) {
+    cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream);
+    return fail(h, LBM_ECUDA, "a step kernel gave up waiting for its staged rows (results since the last check are invalid)");
+  }
+  return LBM_OK;
+}
+
 template <typename T>
 static int run_macro(lbm_handle* h) {
   int rc = ensure_macro(h);
@@ -247,6 +263,8 @@ static int run_diag(lbm_handle* h) {
   double r[DIAG_FIELDS];
   CUDA_TRY(h, cudaMemcpyAsync(r, h->ddiag, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  int rc2 = check_device_flag(h);
+  if (rc2) return rc2;
   const double n = r[5];
   h->diag[0] = (double)h->t;
   h->diag[1] = r[0];
@@ -267,7 +285,10 @@ static int do_step(lbm_handle* h, int64_t n) {
     const bool due = de > 0 && ((h->t + 1) % de == 0);
     Bufs<T> B = bufs_now<T>(h);
     B.phi_prev = due ? (T*)h->phi_prev : nullptr;
-    CUDA_TRY(h, launch_march<T>(h->prm.phase_model, MODE_STEP, P, B, h->stream));
+    cudaError_t e = cudaErrorNotSupported;
+    if (h->use_tma && h->prm.phase_model == LBM_AC) e = launch_step_tma<T>(P, B, h->derr, h->stream);
+    if (e == cudaErrorNotSupported) e = launch_march<T>(h->prm.phase_model, MODE_STEP, P, B, h->stream);
+    CUDA_TRY(h, e);
     h->cur ^= 1;
     h->t += 1;
     if (due) {
@@ -327,7 +348,7 @@ static int export_planes(lbm_handle* h, const T* src, int planes, double add0, d
     CUDA_TRY(h, cudaMemcpyAsync(out + k * N, h->dstage, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   }
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  return LBM_OK;
+  return check_device_flag(h);
 }
 
 template <typename T>
@@ -429,10 +450,13 @@ int lbm_create(const lbm_params* params, void* stream, const lbm_allocator* allo
     h->have_alloc = true;
   }
   h->prec = params->precision;
+  h->use_tma = (params->flags & LBM_FLAG_NO_TMA) == 0;
   h->esize = h->prec == LBM_FP64 ? 8 : 4;
   h->nx = params->nx;
   h->ny = params->ny;
-  h->pitch = (h->nx + 31) / 32 * 32;
+  // rows carry XPAD pad elements per side; the pitch leaves room for a
+  // 16-byte rounded bulk copy of the last strip's segment
+  h->pitch = (h->nx + 2 * XPAD + 4 + 31) / 32 * 32;
   h->plane = (long long)h->pitch * h->ny;
   derive(h);
   const size_t pl = (size_t)h->plane * h->esize;
@@ -445,6 +469,7 @@ int lbm_create(const lbm_params* params, void* stream, const lbm_allocator* allo
   h->nparts = (int)std::min<long long>((N + DIAG_THREADS - 1) / DIAG_THREADS, 152 * 8);
   ok = ok && (h->dpart = (double*)dev_alloc(h, (size_t)h->nparts * DIAG_FIELDS * sizeof(double)));
   ok = ok && (h->ddiag = (double*)dev_alloc(h, DIAG_FIELDS * sizeof(double)));
+  ok = ok && (h->derr = (int*)dev_alloc(h, sizeof(int)));
   if (!ok) {
     std::string msg = "device allocation of " + std::to_string(h->bytes) + " bytes failed";
     lbm_destroy(h);

@@ -51,6 +51,13 @@ enum { SIDE_LEFT = 0, SIDE_RIGHT = 1, SIDE_BOTTOM = 2, SIDE_TOP = 3 };
 constexpr int BX = 128;  // threads per block = columns per strip
 constexpr int LY = 64;   // rows per block
 constexpr int RING = 8;  // shared-memory ring of phi rows (power of two)
+// Each stored row has XPAD pad elements on either side of its nx nodes:
+// element (x, y) of a plane sits at y * pitch + XPAD + x, x in [-XPAD, nx + XPAD).
+// With a periodic x boundary the pads of the population planes hold copies
+// of the XPAD nodes at the opposite edge (written together with the nodes),
+// so a 16-byte aligned bulk copy of [x0 - XPAD, x0 + BX + XPAD) of a row
+// carries its own halo.
+constexpr int XPAD = 4;
 
 // Per-run constants, in the arithmetic type.
 template <typename T>
@@ -88,6 +95,11 @@ struct Bufs {
 
 __host__ __device__ constexpr int slot_of(int r) { return (r + 2 * RING) & (RING - 1); }
 
+template <typename T>
+__device__ __forceinline__ long long at(const Phys<T>& P, int x, int y) {
+  return (long long)y * P.pitch + XPAD + x;
+}
+
 // ---------------------------------------------------------------------------
 // Pull the nine populations of node (x, r) from the post-collision planes,
 // with periodic wrap or half-way bounce-back at walls (Sec. 4).
@@ -104,16 +116,16 @@ __device__ __forceinline__ void pull9(const T* __restrict__ buf, const Phys<T>& 
   const long long pl = P.plane;
   const long long rc = (long long)r * P.pitch, rm = (long long)ym * P.pitch,
                   rp = (long long)yp * P.pitch;
-  const long long c = rc + x;
+  const long long c = rc + XPAD + x;
   out[0] = buf[c];
-  out[1] = buf[bxm ? 3 * pl + c : 1 * pl + rc + xm];
-  out[2] = buf[bym ? 4 * pl + c : 2 * pl + rm + x];
-  out[3] = buf[bxp ? 1 * pl + c : 3 * pl + rc + xp];
-  out[4] = buf[byp ? 2 * pl + c : 4 * pl + rp + x];
-  out[5] = buf[(bxm || bym) ? 7 * pl + c : 5 * pl + rm + xm];
-  out[6] = buf[(bxp || bym) ? 8 * pl + c : 6 * pl + rm + xp];
-  out[7] = buf[(bxp || byp) ? 5 * pl + c : 7 * pl + rp + xp];
-  out[8] = buf[(bxm || byp) ? 6 * pl + c : 8 * pl + rp + xm];
+  out[1] = buf[bxm ? 3 * pl + c : 1 * pl + rc + XPAD + xm];
+  out[2] = buf[bym ? 4 * pl + c : 2 * pl + rm + XPAD + x];
+  out[3] = buf[bxp ? 1 * pl + c : 3 * pl + rc + XPAD + xp];
+  out[4] = buf[byp ? 2 * pl + c : 4 * pl + rp + XPAD + x];
+  out[5] = buf[(bxm || bym) ? 7 * pl + c : 5 * pl + rm + XPAD + xm];
+  out[6] = buf[(bxp || bym) ? 8 * pl + c : 6 * pl + rm + XPAD + xp];
+  out[7] = buf[(bxp || byp) ? 5 * pl + c : 7 * pl + rp + XPAD + xp];
+  out[8] = buf[(bxm || byp) ? 6 * pl + c : 8 * pl + rp + XPAD + xm];
 }
 
 template <typename T>
@@ -154,6 +166,7 @@ __device__ __forceinline__ T wall_ghost(const Phys<T>& P, int side, T phi1, T ph
 // ---------------------------------------------------------------------------
 template <typename T, int MODEL, int MODE>
 __device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, long long idx,
+                                            long long padL, long long padR,
                                             const T phi9[9], const T mu9[9], const T f[9],
                                             const T g[9], const T h[5], T u_in, T v_in, T p_in) {
   const T phi = phi9[0];
@@ -393,6 +406,29 @@ __device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, 
     B.fout[i * P.plane + idx] = fs[i];
     B.gout[i * P.plane + idx] = gs[i];
   }
+  if (padL >= 0) {  // periodic copy in the left pad
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      B.fout[i * P.plane + padL] = fs[i];
+      B.gout[i * P.plane + padL] = gs[i];
+    }
+  }
+  if (padR >= 0) {  // periodic copy in the right pad
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      B.fout[i * P.plane + padR] = fs[i];
+      B.gout[i * P.plane + padR] = gs[i];
+    }
+  }
+}
+
+// Pad positions that mirror node (x, y) under a periodic x boundary (-1: none).
+template <typename T>
+__device__ __forceinline__ void pad_slots(const Phys<T>& P, int x, int y, long long& padL, long long& padR) {
+  padL = padR = -1;
+  if (P.wall_x) return;
+  if (x >= P.nx - XPAD) padL = at(P, x - P.nx, y);
+  if (x < XPAD) padR = at(P, x + P.nx, y);
 }
 
 // ---------------------------------------------------------------------------
@@ -553,7 +589,7 @@ __global__ void __launch_bounds__(BX) k_march(const Phys<T> P, const Bufs<T> B) 
     T g[9] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
     T h[5] = {T(0), T(0), T(0), T(0), T(0)};
     T uin = T(0), vin = T(0), pin = T(0);
-    const long long idx = (long long)y * P.pitch + x;
+    const long long idx = at(P, x, y);
     if (active) {
       if (MODE == MODE_INIT) {
         const long long di = (long long)y * nx + x;
@@ -617,13 +653,301 @@ __global__ void __launch_bounds__(BX) k_march(const Phys<T> P, const Bufs<T> B) 
         mu9[7] = smu[sm][cm - 1];
         mu9[8] = smu[sm][cm + 1];
       }
-      node_update<T, MODEL, MODE>(P, B, idx, phi9, mu9, fq[0], g, h, uin, vin, pin);
+      long long padL, padR;
+      pad_slots(P, x, y, padL, padR);
+      node_update<T, MODEL, MODE>(P, B, idx, padL, padR, phi9, mu9, fq[0], g, h, uin, vin, pin);
     }
     // advance the queue of pulled f
 #pragma unroll
     for (int q = 0; q < R; ++q)
 #pragma unroll
       for (int i = 0; i < 9; ++i) fq[q][i] = fq[q + 1][i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// TMA-staged fused step (Allen-Cahn, MODE_STEP): the hot path.
+//
+// Same per-node arithmetic as k_march, with the population rows brought in
+// by the Tensor Memory Accelerator: one elected thread issues, per source
+// row, nine 1-D bulk copies (cp.async.bulk) of the aligned segment
+// [x0 - XPAD, x0 + BX + XPAD) of the f planes, and nine of the g planes, into
+// shared-memory rings whose slots complete on an mbarrier (expect_tx bytes).
+// Rows are requested one march step ahead, so the HBM latency of row y + 1
+// overlaps the arithmetic of row y without holding the data in registers;
+// the pull shifts become shared-memory index offsets and the halo columns
+// arrive with the row.  Every wait is bounded: on time-out the block records
+// the failure in *err (the host turns it into LBM_ECUDA), lets the copies it
+// issued land (again with a bound) and returns.
+//
+// Ring depths: f rows y-1 .. y+3 are live while row y is processed (pulls of
+// row y and phi of row y+2), and row y+4 is in flight: 6 slots.  g rows
+// y-1 .. y+1 live, y+2 in flight: 4 slots.
+// ---------------------------------------------------------------------------
+constexpr int SEG = BX + 2 * XPAD;  // staged columns per plane row
+constexpr int RF = 6, RG = 4;
+// Each try_wait suspends for at most ~1 us (the hint), so a wait gives up
+// after about a second; a normal row arrives within microseconds.
+constexpr long long MBAR_SPIN_LIMIT = 1LL << 20;
+constexpr long long MBAR_DRAIN_LIMIT = 1LL << 10;
+
+template <typename T>
+struct TmaLayout {
+  static constexpr size_t f_off = 0;
+  static constexpr size_t g_off = f_off + sizeof(T) * RF * 9 * SEG;
+  static constexpr size_t phi_off = g_off + sizeof(T) * RG * 9 * SEG;
+  static constexpr size_t bar_off = phi_off + sizeof(T) * RING * (BX + 2);
+  static constexpr size_t bytes = bar_off + 8 * (RF + RG);
+  static_assert(g_off % 16 == 0 && phi_off % 16 == 0 && bar_off % 8 == 0, "smem layout alignment");
+  static_assert((SEG * sizeof(T)) % 16 == 0, "bulk-copy rows must be 16-byte multiples");
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.release.cta.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+          smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  long long limit = MBAR_SPIN_LIMIT) {
+  for (long long it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// Pull of the node in staged column c (row rr) from the source-row slots
+// rm, r0, rp (rows rr-1, rr, rr+1); bounce-back where the source lies beyond
+// a wall.  xg is the node's global column (for the x-wall test).
+template <typename T>
+__device__ __forceinline__ void pull_staged(const T* rm, const T* r0, const T* rp, int c, bool bxm, bool bxp,
+                                            bool bym, bool byp, T out[9]) {
+  out[0] = r0[0 * SEG + c];
+  out[1] = bxm ? r0[3 * SEG + c] : r0[1 * SEG + c - 1];
+  out[2] = bym ? r0[4 * SEG + c] : rm[2 * SEG + c];
+  out[3] = bxp ? r0[1 * SEG + c] : r0[3 * SEG + c + 1];
+  out[4] = byp ? r0[2 * SEG + c] : rp[4 * SEG + c];
+  out[5] = (bxm || bym) ? r0[7 * SEG + c] : rm[5 * SEG + c - 1];
+  out[6] = (bxp || bym) ? r0[8 * SEG + c] : rm[6 * SEG + c + 1];
+  out[7] = (bxp || byp) ? r0[5 * SEG + c] : rp[7 * SEG + c + 1];
+  out[8] = (bxm || byp) ? r0[6 * SEG + c] : rp[8 * SEG + c - 1];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX, (sizeof(T) == 4) ? 4 : 2)
+    k_step_tma(const Phys<T> P, const Bufs<T> B, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  T* const sf = reinterpret_cast<T*>(smem + TmaLayout<T>::f_off);    // [RF][9][SEG]
+  T* const sg = reinterpret_cast<T*>(smem + TmaLayout<T>::g_off);    // [RG][9][SEG]
+  T* const sp = reinterpret_cast<T*>(smem + TmaLayout<T>::phi_off);  // [RING][BX + 2]
+  uint64_t* const barF = reinterpret_cast<uint64_t*>(smem + TmaLayout<T>::bar_off);
+  uint64_t* const barG = barF + RF;
+
+  const int tid = threadIdx.x;
+  const int nx = P.nx, ny = P.ny;
+  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * LY;
+  const int w = min(BX, nx - x0);
+  const int y1 = min(y0 + LY, ny);
+  const bool active = tid < w;
+  const int x = x0 + tid;
+  const bool wx = P.wall_x != 0, wy = P.wall_y != 0;
+  const int fbase = y0 - 2, gbase = y0 - 1;  // first staged f / g row
+  constexpr int VE = 16 / (int)sizeof(T);
+  const uint32_t seg_bytes = (uint32_t)(((w + 2 * XPAD + VE - 1) / VE) * VE * (int)sizeof(T));
+  const int f_last = y1 + 1, g_last = y1;  // last f / g row any output row needs
+
+  if (tid == 0) {
+    for (int k = 0; k < RF + RG; ++k) mbar_init(&barF[k], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  auto wrap_row = [&](int r) { return r < 0 ? r + ny : (r >= ny ? r - ny : r); };
+  // producer side (thread 0 only)
+  auto stage = [&](const T* src, T* slot, uint64_t* bar, int r) {
+    if ((r < 0 || r >= ny) && wy) {  // beyond a wall: nothing to load, complete the phase
+      mbar_arrive(bar);
+      return;
+    }
+    const T* row = src + (long long)wrap_row(r) * P.pitch + x0;  // element x0 - XPAD of the row
+    mbar_arrive_expect_tx(bar, 9u * seg_bytes);
+#pragma unroll 1
+    for (int i = 0; i < 9; ++i) bulk_g2s(slot + i * SEG, row + i * P.plane, seg_bytes, bar);
+  };
+  auto fslot = [&](int r) { return sf + ((r - fbase) % RF) * (9 * SEG); };
+  auto gslot = [&](int r) { return sg + ((r - gbase) % RG) * (9 * SEG); };
+  auto stage_f = [&](int r) { stage(B.fin, fslot(r), &barF[(r - fbase) % RF], r); };
+  auto stage_g = [&](int r) { stage(B.gin, gslot(r), &barG[(r - gbase) % RG], r); };
+  auto wait_f = [&](int r) {
+    const int li = r - fbase;
+    return mbar_wait_bounded(&barF[li % RF], (li / RF) & 1);
+  };
+  auto wait_g = [&](int r) {
+    const int li = r - gbase;
+    return mbar_wait_bounded(&barG[li % RG], (li / RG) & 1);
+  };
+
+  // phi of row r (in the domain, or wrapped) into the phi ring: own column,
+  // left halo (thread 0), right halo (thread w - 1); x-wall ghosts from the
+  // thread's own phi and a second pull of the neighbouring column.
+  auto phi_row = [&](int r) {
+    const int rr = wrap_row(r);
+    const T* rm = fslot(r - 1);
+    const T* r0 = fslot(r);
+    const T* rp = fslot(r + 1);
+    const bool bym = wy && rr == 0, byp = wy && rr == ny - 1;
+    T* dst = sp + slot_of(r) * (BX + 2);
+    if (!active) return;
+    T v[9];
+    pull_staged(rm, r0, rp, tid + XPAD, wx && x == 0, wx && x == nx - 1, bym, byp, v);
+    const T ph = sum9(v);
+    dst[tid + 1] = ph;
+    if (tid == 0) {
+      T hv;
+      if (x0 > 0 || !wx) {
+        pull_staged(rm, r0, rp, XPAD - 1, false, wx && x0 - 1 == nx - 1, bym, byp, v);
+        hv = sum9(v);
+      } else {
+        pull_staged(rm, r0, rp, XPAD + 1, false, wx && 1 == nx - 1, bym, byp, v);
+        hv = wall_ghost(P, SIDE_LEFT, ph, sum9(v));
+      }
+      dst[0] = hv;
+    }
+    if (tid == w - 1) {
+      T hv;
+      if (x0 + w < nx || !wx) {
+        pull_staged(rm, r0, rp, XPAD + w, wx && x0 + w == 0, wx && x0 + w == nx - 1, bym, byp, v);
+        hv = sum9(v);
+      } else {
+        pull_staged(rm, r0, rp, XPAD + w - 2, wx && nx - 2 == 0, false, bym, byp, v);
+        hv = wall_ghost(P, SIDE_RIGHT, ph, sum9(v));
+      }
+      dst[w + 1] = hv;
+    }
+  };
+  auto ghost_row = [&](int rg, int r1, int r2, int side) {
+    T* d = sp + slot_of(rg) * (BX + 2);
+    const T* a = sp + slot_of(r1) * (BX + 2);
+    const T* b = sp + slot_of(r2) * (BX + 2);
+    for (int j = tid; j < w + 2; j += BX) d[j] = wall_ghost(P, side, a[j], b[j]);
+  };
+
+  bool ok = true;
+  // ---------------------------------------------------------------- prologue
+  if (tid == 0) {
+    for (int r = fbase; r <= min(y0 + 3, f_last); ++r) stage_f(r);
+    for (int r = gbase; r <= min(y0 + 1, g_last); ++r) stage_g(r);
+  }
+  for (int r = fbase; r <= min(y0 + 2, f_last); ++r) ok = wait_f(r) && ok;
+  for (int r = y0 - 1; r <= y0 + 1; ++r)
+    if (r <= y1 && ((r >= 0 && r < ny) || !wy)) phi_row(r);
+  bool failed = __syncthreads_or(!ok);
+  if (!failed && wy && (y0 == 0 || y0 + 1 >= ny)) {
+    if (y0 == 0) ghost_row(-1, 0, 1, SIDE_BOTTOM);
+    if (y0 + 1 >= ny) ghost_row(ny, ny - 1, ny - 2, SIDE_TOP);
+    __syncthreads();
+  }
+  T h[5] = {T(0), T(0), T(0), T(0), T(0)};
+  if (active) {
+    const long long id = at(P, x, y0);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) h[k] = B.hist[k * P.plane + id];
+  }
+
+  // ---------------------------------------------------------------- march
+  for (int y = y0; y < y1 && !failed; ++y) {
+    ok = true;
+    if (y + 3 <= f_last) ok = wait_f(y + 3) && ok;
+    if (y + 1 <= g_last) ok = wait_g(y + 1) && ok;
+    const int r2 = y + 2;
+    if (r2 <= y1) {
+      if (r2 < ny || !wy) phi_row(r2);
+      else if (r2 == ny) ghost_row(ny, ny - 1, ny - 2, SIDE_TOP);  // rows ny-1, ny-2 ready since the last barrier
+    }
+    failed = __syncthreads_or(!ok);
+    if (failed) break;
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      if (y + 4 <= f_last) stage_f(y + 4);
+      if (y + 2 <= g_last) stage_g(y + 2);
+    }
+    T hn[5] = {T(0), T(0), T(0), T(0), T(0)};
+    if (active && y + 1 < y1) {
+      const long long id = at(P, x, y + 1);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) hn[k] = B.hist[k * P.plane + id];
+    }
+    if (active) {
+      const T* pm = sp + slot_of(y - 1) * (BX + 2);
+      const T* p0 = sp + slot_of(y) * (BX + 2);
+      const T* pp = sp + slot_of(y + 1) * (BX + 2);
+      const int c = tid + 1;
+      T phi9[9];
+      phi9[0] = p0[c];
+      phi9[1] = p0[c + 1];
+      phi9[2] = pp[c];
+      phi9[3] = p0[c - 1];
+      phi9[4] = pm[c];
+      phi9[5] = pp[c + 1];
+      phi9[6] = pp[c - 1];
+      phi9[7] = pm[c - 1];
+      phi9[8] = pm[c + 1];
+      const bool bxm = wx && x == 0, bxp = wx && x == nx - 1;
+      const bool bym = wy && y == 0, byp = wy && y == ny - 1;
+      T f[9], g[9];
+      pull_staged(fslot(y - 1), fslot(y), fslot(y + 1), tid + XPAD, bxm, bxp, bym, byp, f);
+      pull_staged(gslot(y - 1), gslot(y), gslot(y + 1), tid + XPAD, bxm, bxp, bym, byp, g);
+      long long padL, padR;
+      pad_slots(P, x, y, padL, padR);
+      node_update<T, MODEL_AC, MODE_STEP>(P, B, at(P, x, y), padL, padR, phi9, phi9, f, g, h, T(0), T(0), T(0));
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) h[k] = hn[k];
+  }
+  if (failed) {
+    // record, then let every copy this block issued land (bounded) before
+    // the block's shared memory is released
+    if (tid == 0) {
+      atomicOr(err, 1);
+      for (int k = 0; k < RF + RG; ++k) {
+        for (int q = 0; q < 2; ++q) mbar_wait_bounded(&barF[k], q, MBAR_DRAIN_LIMIT);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -638,7 +962,7 @@ __global__ void k_pull(const Phys<T> P, const T* __restrict__ in, T* __restrict_
   if (x >= P.nx) return;
   T v[9];
   pull9(in, P, x, y, v);
-  const long long idx = (long long)y * P.pitch + x;
+  const long long idx = at(P, x, y);
 #pragma unroll
   for (int i = 0; i < 9; ++i) out[i * P.plane + idx] = v[i];
 }
@@ -654,7 +978,7 @@ __global__ void k_unstream(const Phys<T> P, const T* __restrict__ in, T* __restr
   const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
   const int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
   const int op[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-  const long long idx = (long long)y * P.pitch + x;
+  const long long idx = at(P, x, y);
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     int sx = x - cx[i], sy = y - cy[i];
@@ -662,8 +986,12 @@ __global__ void k_unstream(const Phys<T> P, const T* __restrict__ in, T* __restr
     if (sx < 0 || sx >= P.nx) { if (P.wall_x) wall = true; else sx = (sx + P.nx) % P.nx; }
     if (sy < 0 || sy >= P.ny) { if (P.wall_y) wall = true; else sy = (sy + P.ny) % P.ny; }
     const T val = in[i * P.plane + idx];
-    if (wall) out[op[i] * P.plane + idx] = val;
-    else out[i * P.plane + (long long)sy * P.pitch + sx] = val;
+    const int dx = wall ? x : sx, dy = wall ? y : sy, di = wall ? op[i] : i;
+    out[di * P.plane + at(P, dx, dy)] = val;
+    long long padL, padR;
+    pad_slots(P, dx, dy, padL, padR);
+    if (padL >= 0) out[di * P.plane + padL] = val;
+    if (padR >= 0) out[di * P.plane + padR] = val;
   }
 }
 
@@ -675,7 +1003,7 @@ __global__ void k_export(const Phys<T> P, const T* __restrict__ in, double* __re
   const int xx = blockIdx.x * blockDim.x + threadIdx.x;
   const int yy = blockIdx.y;
   if (xx >= w) return;
-  const long long src = (long long)(y0 + yy) * P.pitch + (x0 + xx);
+  const long long src = at(P, x0 + xx, y0 + yy);
   for (int k = 0; k < planes; ++k)
     out[(long long)k * w * hgt + (long long)yy * w + xx] =
         double(in[k * P.plane + src]) + (k == 0 ? add0 : 0.0);
@@ -688,7 +1016,7 @@ __global__ void k_import(const Phys<T> P, const double* __restrict__ in, T* __re
   const int y = blockIdx.y;
   if (x >= P.nx) return;
   for (int k = 0; k < planes; ++k)
-    out[k * P.plane + (long long)y * P.pitch + x] =
+    out[k * P.plane + at(P, x, y)] =
         T(in[(long long)k * P.nx * P.ny + (long long)y * P.nx + x] - (k == 0 ? sub0 : 0.0));
 }
 
@@ -740,7 +1068,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(const Phys<T> P, 
   for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(n / P.nx), x = (int)(n - (long long)y * P.nx);
-    const long long id = (long long)y * P.pitch + x;
+    const long long id = at(P, x, y);
     const double phi = double(mac[MAC_PHI * pl + id]);
     const double u = double(mac[MAC_UX * pl + id]), vv = double(mac[MAC_UY * pl + id]);
     const double um2 = u * u + vv * vv;
@@ -758,7 +1086,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(const Phys<T> P, 
       int xn = x + cx[k], yn = y + cy[k];
       xn = xn < 0 ? xn + P.nx : (xn >= P.nx ? xn - P.nx : xn);
       yn = yn < 0 ? yn + P.ny : (yn >= P.ny ? yn - P.ny : yn);
-      const long long q = (long long)yn * P.pitch + xn;
+      const long long q = at(P, xn, yn);
       const double rq = double(mac[MAC_RHO * pl + q]);
       const double Jx = rq * double(mac[MAC_UX * pl + q]) + double(mac[MAC_MCX * pl + q]);
       const double Jy = rq * double(mac[MAC_UY * pl + q]) + double(mac[MAC_MCY * pl + q]);

@@ -11,6 +11,10 @@ namespace pflbm {
 
 template <typename T>
 cudaError_t launch_march(int model, int mode, const Phys<T>& P, const Bufs<T>& B, cudaStream_t s);
+// TMA-staged Allen-Cahn step (returns cudaErrorNotSupported when the grid is
+// too narrow for it; the caller then uses launch_march)
+template <typename T>
+cudaError_t launch_step_tma(const Phys<T>& P, const Bufs<T>& B, int* err, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pull(const Phys<T>& P, const T* in, T* out, cudaStream_t s);
 template <typename T>

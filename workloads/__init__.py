@@ -107,6 +107,7 @@ class Params:
     gravity_mode: int = GRAV_CONST
     bc: tuple = (BC_PERIODIC, BC_PERIODIC, BC_PERIODIC, BC_PERIODIC)
     diag_every: int = 0
+    flags: int = 0  # library option bits (not part of the method)
     phiA: float = 1.0
     phiB: float = 0.0
     rhoA: float = 1.0
