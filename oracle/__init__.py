@@ -66,7 +66,7 @@ def build(force: bool = False) -> str:
                 and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
             return _LIB
         tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-std=c99", "-O2", "-fno-fast-math", "-fPIC", "-shared", "-fopenmp",
+        cmd = ["gcc", "-std=c99", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fPIC", "-shared", "-fopenmp",
                _SRC, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)

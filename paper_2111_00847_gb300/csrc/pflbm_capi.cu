@@ -36,6 +36,7 @@ struct lbm_handle {
   double* ddiag = nullptr;
   int* derr = nullptr;  // device flag raised by a kernel whose bounded wait timed out
   bool use_tma = true;
+  bool unit_rates = false;  // the rates the paper leaves at 1 are 1
   int nparts = 0;
   double diag[LBM_NDIAG] = {0};
   int64_t t = 0;
@@ -146,6 +147,11 @@ static void derive(lbm_handle* h) {
     h->sf[k] = std::isnan(P.s_f[k]) ? ((k == 3 || k == 5) ? 1.0 / (3.0 * P.mobility / P.eta + 0.5) : 1.0) : P.s_f[k];
     h->sg_node[k] = std::isnan(P.s_g[k]) && (k == 7 || k == 8);
     h->sg[k] = std::isnan(P.s_g[k]) ? 1.0 : P.s_g[k];
+  }
+  h->unit_rates = true;
+  for (int k = 0; k < 9; ++k) {
+    if (k != 3 && k != 5 && h->sf[k] != 1.0) h->unit_rates = false;
+    if ((k <= 3 || k == 5) && h->sg[k] != 1.0) h->unit_rates = false;
   }
   // App. C: H = (s_g^2 - s_g^0) / (9 s_g^0 s_g^2)
   h->H = (h->sg[2] - h->sg[0]) / (9.0 * h->sg[0] * h->sg[2]);
@@ -286,7 +292,8 @@ static int do_step(lbm_handle* h, int64_t n) {
     Bufs<T> B = bufs_now<T>(h);
     B.phi_prev = due ? (T*)h->phi_prev : nullptr;
     cudaError_t e = cudaErrorNotSupported;
-    if (h->use_tma && h->prm.phase_model == LBM_AC) e = launch_step_tma<T>(P, B, h->derr, h->stream);
+    if (h->use_tma && h->prm.phase_model == LBM_AC)
+      e = launch_step_tma<T>(P, B, h->derr, h->unit_rates, h->stream);
     if (e == cudaErrorNotSupported) e = launch_march<T>(h->prm.phase_model, MODE_STEP, P, B, h->stream);
     CUDA_TRY(h, e);
     h->cur ^= 1;

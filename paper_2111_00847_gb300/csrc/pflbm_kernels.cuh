@@ -95,6 +95,20 @@ struct Bufs {
 
 __host__ __device__ constexpr int slot_of(int r) { return (r + 2 * RING) & (RING - 1); }
 
+// Division and the normal's 1/max(|grad phi|, delta): IEEE in FP64 (the
+// path held to 1e-12 against the oracle), hardware approximations in FP32
+// (<= 2 ulp, far inside the FP32 tolerance) where they save the slow path
+// of an IEEE divide.
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double inv_floor_norm(double g2, double delta) {
+  const double gm = sqrt(g2);
+  return 1.0 / (gm > delta ? gm : delta);
+}
+__device__ __forceinline__ float inv_floor_norm(float g2, float delta) {
+  return rsqrtf(fmaxf(g2, delta * delta));
+}
+
 template <typename T>
 __device__ __forceinline__ long long at(const Phys<T>& P, int x, int y) {
   return (long long)y * P.pitch + XPAD + x;
@@ -164,7 +178,11 @@ __device__ __forceinline__ T wall_ghost(const Phys<T>& P, int side, T phi1, T ph
 // Per-node update.  phi9 / mu9: values at x + c_i (D2Q9 order), f, g: pulled
 // populations, h: chi(t-1).  Writes the outputs of the mode.
 // ---------------------------------------------------------------------------
-template <typename T, int MODEL, int MODE>
+// UR ("unit rates"): the relaxation rates of Sec. 4 that the paper leaves at
+// 1 are 1 (s_f^k for k != 3, 5 and s_g^k for k = 0, 1, 2, 3, 5); those
+// moments then relax to m^eq + m_src / 2 without reading the populations'
+// own moments, which the general path (UR = false) computes and relaxes.
+template <typename T, int MODEL, int MODE, bool UR = false>
 __device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, long long idx,
                                             long long padL, long long padR,
                                             const T phi9[9], const T mu9[9], const T f[9],
@@ -185,8 +203,7 @@ __device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, 
     // (delta_n = 1e-3 dphi / W: the unit normal across the interface, and a
     // Lipschitz function of grad phi in the bulk where |grad phi| -> 0)
     lam = P.lam_coef * (P.phiA - phi) * (phi - P.phiB);
-    const T gnorm = sqrt(gx * gx + gy * gy);
-    const T inv = T(1) / (gnorm > P.n_delta ? gnorm : P.n_delta);
+    const T inv = inv_floor_norm(gx * gx + gy * gy, P.n_delta);
     nnx = gx * inv;
     nny = gy * inv;
     Dx = gx - lam * nnx;
@@ -216,7 +233,7 @@ __device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, 
     v = v_in;
   } else {
     // Eq. (22b): rho u = sum c_i g_i + F/2
-    const T irho = T(1) / rho;
+    const T irho = fdiv(T(1), rho);
     u = ((g13 + gdx) + T(0.5) * Fx) * irho;
     v = ((g24 + gdy) + T(0.5) * Fy) * irho;
   }
@@ -263,10 +280,10 @@ __device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, 
     T snode;
     if (!P.visc_inverse) {
       const T muv = frac * (P.muA - P.muB) + P.muB;
-      snode = rho / (T(3) * muv + T(0.5) * rho);
+      snode = fdiv(rho, T(3) * muv + T(0.5) * rho);
     } else {
       const T inu = frac * (P.inuA - P.inuB) + P.inuB;
-      snode = inu / (T(3) + T(0.5) * inu);
+      snode = fdiv(inu, T(3) + T(0.5) * inu);
     }
     if (P.sg7_node) s7 = snode;
     if (P.sg8_node) s8 = snode;
@@ -327,6 +344,25 @@ __device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, 
     fs[0] = (phi - e1 + e2) * T(1.0 / 9.0);
     fs[1] = a + X; fs[3] = a - X; fs[2] = a + Y; fs[4] = a - Y;
     fs[5] = b + Xd + Yd; fs[6] = b - Xd + Yd; fs[7] = b - Xd - Yd; fs[8] = b + Xd - Yd;
+  } else if (UR) {
+    // only j_x, j_y (moments 3, 5) relax at s_f^{3,5}; the others take
+    // m^eq + m_R / 2 (m_R vanishes in moments 0-2, 7, 8)
+    const T f13 = f[1] - f[3], f24 = f[2] - f[4];
+    const T fdx = (f[5] - f[7]) + (f[8] - f[6]);
+    const T fdy = (f[5] - f[7]) + (f[6] - f[8]);
+    const T m3 = f13 + fdx, m5 = f24 + fdy;
+    const T s3 = m3 + P.sf[3] * (phu - m3) + P.hf[3] * Xx;
+    const T s5 = m5 + P.sf[5] * (phv - m5) + P.hf[5] * Xy;
+    const T s4 = -phu - T(0.5) * Xx;
+    const T s6 = -phv - T(0.5) * Xy;
+    const T a = phi * T(1.0 / 9.0) - e1 * T(1.0 / 36.0) - e2 * T(1.0 / 18.0);
+    const T b = phi * T(1.0 / 9.0) + e1 * T(1.0 / 18.0) + e2 * T(1.0 / 36.0);
+    const T X = (s3 - s4) * T(1.0 / 6.0), Y = (s5 - s6) * T(1.0 / 6.0);
+    const T Xd = s3 * T(1.0 / 6.0) + s4 * T(1.0 / 12.0);
+    const T Yd = s5 * T(1.0 / 6.0) + s6 * T(1.0 / 12.0);
+    fs[0] = (phi - e1 + e2) * T(1.0 / 9.0);
+    fs[1] = a + X; fs[3] = a - X; fs[2] = a + Y; fs[4] = a - Y;
+    fs[5] = b + Xd + Yd; fs[6] = b - Xd + Yd; fs[7] = b - Xd - Yd; fs[8] = b + Xd - Yd;
   } else {
     const T fa = (f[1] + f[3]) + (f[2] + f[4]);
     const T fb = (f[5] + f[7]) + (f[6] + f[8]);
@@ -383,6 +419,15 @@ __device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, 
     if (MODE == MODE_INIT) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) m[k] = eq[k];
+    } else if (UR) {
+      // moments 0, 1, 2, 3, 5 relax at rate 1: m^eq + m_F / 2
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (k != 4) m[k] = eq[k] + T(0.5) * src[k];
+      m[4] = m[4] + P.sg[4] * (eq[4] - m[4]) + P.hg[4] * src[4];
+      m[6] = m[6] + P.sg[6] * (eq[6] - m[6]) + P.hg[6] * src[6];
+      m[7] = m[7] + s7 * (eq[7] - m[7]) + (T(1) - T(0.5) * s7) * src[7];
+      m[8] = m[8] + s8 * (eq[8] - m[8]) + (T(1) - T(0.5) * s8) * src[8];
     } else {
 #pragma unroll
       for (int k = 0; k < 7; ++k) m[k] = m[k] + P.sg[k] * (eq[k] - m[k]) + P.hg[k] * src[k];
@@ -767,7 +812,7 @@ __device__ __forceinline__ void pull_staged(const T* rm, const T* r0, const T* r
   out[8] = (bxm || byp) ? r0[6 * SEG + c] : rp[8 * SEG + c - 1];
 }
 
-template <typename T>
+template <typename T, bool UR>
 __global__ void __launch_bounds__(BX, (sizeof(T) == 4) ? 4 : 2)
     k_step_tma(const Phys<T> P, const Bufs<T> B, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -789,6 +834,7 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4) ? 4 : 2)
   constexpr int VE = 16 / (int)sizeof(T);
   const uint32_t seg_bytes = (uint32_t)(((w + 2 * XPAD + VE - 1) / VE) * VE * (int)sizeof(T));
   const int f_last = y1 + 1, g_last = y1;  // last f / g row any output row needs
+  const bool edge_x = wx && (x0 == 0 || x0 + w == nx);  // strip touches an x wall
 
   if (tid == 0) {
     for (int k = 0; k < RF + RG; ++k) mbar_init(&barF[k], 1);
@@ -833,7 +879,10 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4) ? 4 : 2)
     T* dst = sp + slot_of(r) * (BX + 2);
     if (!active) return;
     T v[9];
-    pull_staged(rm, r0, rp, tid + XPAD, wx && x == 0, wx && x == nx - 1, bym, byp, v);
+    if (edge_x || bym || byp)
+      pull_staged(rm, r0, rp, tid + XPAD, wx && x == 0, wx && x == nx - 1, bym, byp, v);
+    else
+      pull_staged(rm, r0, rp, tid + XPAD, false, false, false, false, v);
     const T ph = sum9(v);
     dst[tid + 1] = ph;
     if (tid == 0) {
@@ -926,14 +975,20 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4) ? 4 : 2)
       phi9[6] = pp[c - 1];
       phi9[7] = pm[c - 1];
       phi9[8] = pm[c + 1];
-      const bool bxm = wx && x == 0, bxp = wx && x == nx - 1;
       const bool bym = wy && y == 0, byp = wy && y == ny - 1;
       T f[9], g[9];
-      pull_staged(fslot(y - 1), fslot(y), fslot(y + 1), tid + XPAD, bxm, bxp, bym, byp, f);
-      pull_staged(gslot(y - 1), gslot(y), gslot(y + 1), tid + XPAD, bxm, bxp, bym, byp, g);
+      if (edge_x || bym || byp) {  // bounce-back links possible (block-uniform test)
+        const bool bxm = wx && x == 0, bxp = wx && x == nx - 1;
+        pull_staged(fslot(y - 1), fslot(y), fslot(y + 1), tid + XPAD, bxm, bxp, bym, byp, f);
+        pull_staged(gslot(y - 1), gslot(y), gslot(y + 1), tid + XPAD, bxm, bxp, bym, byp, g);
+      } else {
+        pull_staged(fslot(y - 1), fslot(y), fslot(y + 1), tid + XPAD, false, false, false, false, f);
+        pull_staged(gslot(y - 1), gslot(y), gslot(y + 1), tid + XPAD, false, false, false, false, g);
+      }
       long long padL, padR;
       pad_slots(P, x, y, padL, padR);
-      node_update<T, MODEL_AC, MODE_STEP>(P, B, at(P, x, y), padL, padR, phi9, phi9, f, g, h, T(0), T(0), T(0));
+      node_update<T, MODEL_AC, MODE_STEP, UR>(P, B, at(P, x, y), padL, padR, phi9, phi9, f, g, h, T(0), T(0),
+                                              T(0));
     }
 #pragma unroll
     for (int k = 0; k < 5; ++k) h[k] = hn[k];

@@ -24,16 +24,21 @@ cudaError_t launch_march(int model, int mode, const Phys<T>& P, const Bufs<T>& B
                            : launch_march_model<T, MODEL_AC>(mode, P, B, s);
 }
 
-template <typename T>
-cudaError_t launch_step_tma(const Phys<T>& P, const Bufs<T>& B, int* err, cudaStream_t s) {
-  if (P.nx < 4 * XPAD) return cudaErrorNotSupported;
+template <typename T, bool UR>
+static cudaError_t launch_step_tma_ur(const Phys<T>& P, const Bufs<T>& B, int* err, cudaStream_t s) {
   // per function and device; cheap next to a step
-  cudaError_t e = cudaFuncSetAttribute(k_step_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_step_tma<T, UR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)TmaLayout<T>::bytes);
   if (e != cudaSuccess) return e;
   const dim3 grid((P.nx + BX - 1) / BX, (P.ny + LY - 1) / LY);
-  k_step_tma<T><<<grid, BX, TmaLayout<T>::bytes, s>>>(P, B, err);
+  k_step_tma<T, UR><<<grid, BX, TmaLayout<T>::bytes, s>>>(P, B, err);
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_step_tma(const Phys<T>& P, const Bufs<T>& B, int* err, bool unit_rates, cudaStream_t s) {
+  if (P.nx < 4 * XPAD) return cudaErrorNotSupported;
+  return unit_rates ? launch_step_tma_ur<T, true>(P, B, err, s) : launch_step_tma_ur<T, false>(P, B, err, s);
 }
 
 static inline dim3 row_grid(int nx, int ny, int threads) { return dim3((nx + threads - 1) / threads, ny); }
@@ -74,7 +79,7 @@ cudaError_t launch_diag(const Phys<T>& P, const T* macro, const T* phi_prev, dou
 
 #define PFLBM_INSTANTIATE(T)                                                                        \
   template cudaError_t launch_march<T>(int, int, const Phys<T>&, const Bufs<T>&, cudaStream_t);   \
-  template cudaError_t launch_step_tma<T>(const Phys<T>&, const Bufs<T>&, int*, cudaStream_t);     \
+  template cudaError_t launch_step_tma<T>(const Phys<T>&, const Bufs<T>&, int*, bool, cudaStream_t); \
   template cudaError_t launch_pull<T>(const Phys<T>&, const T*, T*, cudaStream_t);                \
   template cudaError_t launch_unstream<T>(const Phys<T>&, const T*, T*, cudaStream_t);            \
   template cudaError_t launch_export<T>(const Phys<T>&, const T*, double*, int, double, int, int,  \

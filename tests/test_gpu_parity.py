@@ -329,18 +329,22 @@ def test_full_size_sampled_windows(pk, oracle_mod, n):
 @pytest.mark.parametrize("prec", [W.PREC_FP64, W.PREC_FP32])
 @pytest.mark.parametrize("walls", ["none", "y", "x", "all"])
 @pytest.mark.parametrize("nx,ny", [(300, 150), (16, 70), (257, 129)])
-def test_tma_kernel_matches_register_kernel_bitwise(pk, prec, walls, nx, ny):
-    """The TMA-staged step and the register-pipelined step perform the same
-    per-node arithmetic on the same pulled values: results are identical."""
+def test_tma_kernel_matches_register_kernel(pk, prec, walls, nx, ny):
+    """The TMA-staged step and the register-pipelined step compute the same
+    update from the same pulled values (the TMA kernel relaxes the unit-rate
+    moments as m^eq + m_src/2 instead of m + (m^eq - m) + m_src/2).  After one
+    step they agree to rounding, after 20 steps to the parity bar."""
     case = W.noisy_drop(nx, ny, precision=prec, walls=walls, noise=0.005, u_amp=0.002,
                         theta=(60, 120, 45, 135), gravity=(W.GRAV_RHO, 1e-6, -1e-5))
-    out = []
+    sims = []
     for flags in (0, pk.LBM_FLAG_NO_TMA):
-        prm = case.params.with_(flags=flags)
-        sim = pk.Simulation(prm)
+        sim = pk.Simulation(case.params.with_(flags=flags))
         sim.init_fields(case.phi, case.ux, case.uy, case.p)
-        sim.step(25)
-        out.append((sim.fields(pk.LBM_F_POP), sim.fields(pk.LBM_G_POP), sim.fields(pk.LBM_HIST)))
-        sim.close()
-    for a, b in zip(out[0], out[1]):
-        assert np.array_equal(a, b)
+        sims.append(sim)
+    for steps, tol in ((1, 1e-14 if prec == W.PREC_FP64 else 1e-6), (19, 1e-12 if prec == W.PREC_FP64 else 1e-5)):
+        for sim in sims:
+            sim.step(steps)
+        for which in (pk.LBM_F_POP, pk.LBM_G_POP, pk.LBM_HIST):
+            a, b = sims[0].fields(which), sims[1].fields(which)
+            d = np.abs(a - b).max() / max(np.abs(b).max(), 1e-30)
+            assert d <= tol, (steps, which, d, int((a != b).sum()))
