@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -37,6 +38,7 @@ struct lbm_handle {
   int* derr = nullptr;  // device flag raised by a kernel whose bounded wait timed out
   bool use_tma = true;
   bool unit_rates = false;  // the rates the paper leaves at 1 are 1
+  int tma_variant = 0;      // strip width / prefetch depth of the TMA step kernel
   int nparts = 0;
   double diag[LBM_NDIAG] = {0};
   int64_t t = 0;
@@ -293,7 +295,7 @@ static int do_step(lbm_handle* h, int64_t n) {
     B.phi_prev = due ? (T*)h->phi_prev : nullptr;
     cudaError_t e = cudaErrorNotSupported;
     if (h->use_tma && h->prm.phase_model == LBM_AC)
-      e = launch_step_tma<T>(P, B, h->derr, h->unit_rates, h->stream);
+      e = launch_step_tma<T>(P, B, h->derr, h->unit_rates, h->tma_variant, h->stream);
     if (e == cudaErrorNotSupported) e = launch_march<T>(h->prm.phase_model, MODE_STEP, P, B, h->stream);
     CUDA_TRY(h, e);
     h->cur ^= 1;
@@ -343,30 +345,33 @@ struct Region {
   int x0, y0, w, h;
 };
 
+// planes [k0, k0 + planes) of a set of NP interleaved planes -> host doubles
 template <typename T>
-static int export_planes(lbm_handle* h, const T* src, int planes, double add0, double* out, Region r) {
+static int export_planes(lbm_handle* h, const T* src, int NP, int k0, int planes, double add0, double* out,
+                         Region r) {
   int rc = ensure_stage(h, 1);
   if (rc) return rc;
   const Phys<T> P = make_phys<T>(h);
   const long long N = (long long)r.w * r.h;
   for (int k = 0; k < planes; ++k) {
-    CUDA_TRY(h, launch_export<T>(P, src + (long long)k * h->plane, h->dstage, 1, k == 0 ? add0 : 0.0,
-                                 r.x0, r.y0, r.w, r.h, h->stream));
+    CUDA_TRY(h, launch_export<T>(P, src, NP, k0 + k, h->dstage, k == 0 ? add0 : 0.0, r.x0, r.y0, r.w, r.h,
+                                 h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(out + k * N, h->dstage, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   }
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   return check_device_flag(h);
 }
 
+// host doubles -> all NP planes of an interleaved set (plane 0 minus sub0)
 template <typename T>
-static int import_planes(lbm_handle* h, const double* in, int planes, double sub0, T* dst) {
+static int import_planes(lbm_handle* h, const double* in, int NP, double sub0, T* dst) {
   int rc = ensure_stage(h, 1);
   if (rc) return rc;
   const Phys<T> P = make_phys<T>(h);
   const long long N = (long long)h->nx * h->ny;
-  for (int k = 0; k < planes; ++k) {
+  for (int k = 0; k < NP; ++k) {
     CUDA_TRY(h, cudaMemcpyAsync(h->dstage, in + k * N, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    CUDA_TRY(h, launch_import<T>(P, h->dstage, dst + (long long)k * h->plane, 1, k == 0 ? sub0 : 0.0, h->stream));
+    CUDA_TRY(h, launch_import<T>(P, h->dstage, dst, NP, k, k == 0 ? sub0 : 0.0, h->stream));
   }
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   return LBM_OK;
@@ -381,10 +386,10 @@ static int do_fields(lbm_handle* h, int which, double* out, Region reg) {
       const int s = which == LBM_F_POP ? 0 : 1;
       T* scratch = (T*)h->pops[s][1 - h->cur];
       CUDA_TRY(h, launch_pull<T>(P, (const T*)h->pops[s][h->cur], scratch, h->stream));
-      return export_planes<T>(h, scratch, 9, s == 1 ? h->prm.rho0 : 0.0, out, reg);
+      return export_planes<T>(h, scratch, 9, 0, 9, s == 1 ? h->prm.rho0 : 0.0, out, reg);
     }
     case LBM_HIST:
-      return export_planes<T>(h, (const T*)h->hist, 5, 0.0, out, reg);
+      return export_planes<T>(h, (const T*)h->hist, 5, 0, 5, 0.0, out, reg);
     case LBM_DIAG: {
       int rc = run_diag<T>(h);
       if (rc) return rc;
@@ -408,7 +413,7 @@ static int do_fields(lbm_handle* h, int which, double* out, Region reg) {
   }
   int rc = run_macro<T>(h);
   if (rc) return rc;
-  return export_planes<T>(h, (const T*)h->macro + (long long)plane * h->plane, 1, 0.0, out, reg);
+  return export_planes<T>(h, (const T*)h->macro, NMACRO, plane, 1, 0.0, out, reg);
 }
 
 template <typename T>
@@ -458,6 +463,7 @@ int lbm_create(const lbm_params* params, void* stream, const lbm_allocator* allo
   }
   h->prec = params->precision;
   h->use_tma = (params->flags & LBM_FLAG_NO_TMA) == 0;
+  if (const char* v = std::getenv("PFLBM_TMA_VARIANT")) h->tma_variant = std::atoi(v);
   h->esize = h->prec == LBM_FP64 ? 8 : 4;
   h->nx = params->nx;
   h->ny = params->ny;

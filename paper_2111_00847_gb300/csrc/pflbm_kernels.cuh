@@ -5,9 +5,13 @@
 // (arXiv:2111.00847), Sec. 3 and App. C.  One launch of k_march<T, MODEL,
 // MODE_STEP> advances the whole grid by one time step.
 //
-// Memory layout (HBM).  Populations are structure-of-arrays planes
-// pop[i][y][pitch] (x fastest, pitch a multiple of 32 elements), one plane
-// per D2Q9 direction, two copies (A/B) per population set.  A plane holds
+// Memory layout (HBM).  Populations are structure-of-arrays planes, one per
+// D2Q9 direction, interleaved by rows: element i of node (x, y) of a set of
+// NP planes sits at (y NP + i) pitch + XPAD + x (x fastest, pitch a multiple
+// of 32 elements).  The nine plane-rows of a grid row are thus one pitch
+// apart, so a node's nine stores share one base address with immediate
+// offsets, and a row of all planes is one contiguous block.  There are two
+// copies (A/B) of each population set.  A plane holds
 // the POST-COLLISION value of each node (what it sends); the next step pulls
 // f_i(x) = f_i*(x - c_i) from it, or the reflected f_{opp(i)}*(x) where
 // x - c_i lies beyond a half-way bounce-back wall.  The hydrodynamic g_0 is
@@ -51,8 +55,8 @@ enum { SIDE_LEFT = 0, SIDE_RIGHT = 1, SIDE_BOTTOM = 2, SIDE_TOP = 3 };
 constexpr int BX = 128;  // threads per block = columns per strip
 constexpr int LY = 64;   // rows per block
 constexpr int RING = 8;  // shared-memory ring of phi rows (power of two)
-// Each stored row has XPAD pad elements on either side of its nx nodes:
-// element (x, y) of a plane sits at y * pitch + XPAD + x, x in [-XPAD, nx + XPAD).
+// Each stored row has XPAD pad elements on either side of its nx nodes
+// (x in [-XPAD, nx + XPAD)).
 // With a periodic x boundary the pads of the population planes hold copies
 // of the XPAD nodes at the opposite edge (written together with the nodes),
 // so a 16-byte aligned bulk copy of [x0 - XPAD, x0 + BX + XPAD) of a row
@@ -63,7 +67,7 @@ constexpr int XPAD = 4;
 template <typename T>
 struct Phys {
   int nx, ny, pitch;
-  long long plane;  // ny * pitch
+  long long plane;  // ny * pitch: elements per plane
   int wall_x, wall_y;
   int gravity_mode, visc_inverse, sg7_node, sg8_node;
   T phiA, phiB, phibar, inv_dphi;
@@ -80,12 +84,12 @@ struct Phys {
 
 template <typename T>
 struct Bufs {
-  const T* fin;   // [9] planes, post-collision f of t-1
+  const T* fin;   // 9 interleaved planes, post-collision f of t-1
   const T* gin;
   T* fout;        // STEP: post-collision f of t;  INIT: f^eq per node
   T* gout;
-  T* hist;        // [5] planes
-  T* macro;       // [NMACRO] planes (MACRO)
+  T* hist;        // 5 interleaved planes
+  T* macro;       // NMACRO interleaved planes (MACRO)
   T* phi_prev;    // optional: phi(t) of the stepped time (STEP / HIST)
   const double* iphi;  // INIT inputs, dense [ny][nx]
   const double* iux;
@@ -109,9 +113,10 @@ __device__ __forceinline__ float inv_floor_norm(float g2, float delta) {
   return rsqrtf(fmaxf(g2, delta * delta));
 }
 
+// element k of a set of NP row-interleaved planes at node (x, y)
 template <typename T>
-__device__ __forceinline__ long long at(const Phys<T>& P, int x, int y) {
-  return (long long)y * P.pitch + XPAD + x;
+__device__ __forceinline__ long long ix(const Phys<T>& P, int NP, int k, int x, int y) {
+  return ((long long)y * NP + k) * P.pitch + XPAD + x;
 }
 
 // ---------------------------------------------------------------------------
@@ -127,19 +132,19 @@ __device__ __forceinline__ void pull9(const T* __restrict__ buf, const Phys<T>& 
   if (xp >= P.nx) { if (P.wall_x) bxp = true; else xp -= P.nx; }
   if (ym < 0) { if (P.wall_y) bym = true; else ym += P.ny; }
   if (yp >= P.ny) { if (P.wall_y) byp = true; else yp -= P.ny; }
-  const long long pl = P.plane;
-  const long long rc = (long long)r * P.pitch, rm = (long long)ym * P.pitch,
-                  rp = (long long)yp * P.pitch;
-  const long long c = rc + XPAD + x;
+  const long long pl = P.pitch;  // plane i of a row sits i * pitch after plane 0
+  const long long rc = (long long)r * 9 * pl + XPAD, rm = (long long)ym * 9 * pl + XPAD,
+                  rp = (long long)yp * 9 * pl + XPAD;
+  const long long c = rc + x;
   out[0] = buf[c];
-  out[1] = buf[bxm ? 3 * pl + c : 1 * pl + rc + XPAD + xm];
-  out[2] = buf[bym ? 4 * pl + c : 2 * pl + rm + XPAD + x];
-  out[3] = buf[bxp ? 1 * pl + c : 3 * pl + rc + XPAD + xp];
-  out[4] = buf[byp ? 2 * pl + c : 4 * pl + rp + XPAD + x];
-  out[5] = buf[(bxm || bym) ? 7 * pl + c : 5 * pl + rm + XPAD + xm];
-  out[6] = buf[(bxp || bym) ? 8 * pl + c : 6 * pl + rm + XPAD + xp];
-  out[7] = buf[(bxp || byp) ? 5 * pl + c : 7 * pl + rp + XPAD + xp];
-  out[8] = buf[(bxm || byp) ? 6 * pl + c : 8 * pl + rp + XPAD + xm];
+  out[1] = buf[bxm ? 3 * pl + c : 1 * pl + rc + xm];
+  out[2] = buf[bym ? 4 * pl + c : 2 * pl + rm + x];
+  out[3] = buf[bxp ? 1 * pl + c : 3 * pl + rc + xp];
+  out[4] = buf[byp ? 2 * pl + c : 4 * pl + rp + x];
+  out[5] = buf[(bxm || bym) ? 7 * pl + c : 5 * pl + rm + xm];
+  out[6] = buf[(bxp || bym) ? 8 * pl + c : 6 * pl + rm + xp];
+  out[7] = buf[(bxp || byp) ? 5 * pl + c : 7 * pl + rp + xp];
+  out[8] = buf[(bxm || byp) ? 6 * pl + c : 8 * pl + rp + xm];
 }
 
 template <typename T>
@@ -183,11 +188,11 @@ __device__ __forceinline__ T wall_ghost(const Phys<T>& P, int side, T phi1, T ph
 // moments then relax to m^eq + m_src / 2 without reading the populations'
 // own moments, which the general path (UR = false) computes and relaxes.
 template <typename T, int MODEL, int MODE, bool UR = false>
-__device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, long long idx,
-                                            long long padL, long long padR,
+__device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, int x, int y,
                                             const T phi9[9], const T mu9[9], const T f[9],
                                             const T g[9], const T h[5], T u_in, T v_in, T p_in) {
   const T phi = phi9[0];
+  const long long pc = P.pitch;
   // isotropic gradient and Laplacian, Eqs. (C.9)-(C.10) (c_s^2 = 1/3):
   // grad = 3 sum w_i c_i phi_i ; lap = 6 sum w_i (phi_i - phi)
   const T gx = (phi9[1] - phi9[3]) * T(1.0 / 3.0) + ((phi9[5] - phi9[7]) + (phi9[8] - phi9[6])) * T(1.0 / 12.0);
@@ -263,13 +268,14 @@ __device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, 
 
   if (MODE == MODE_HIST || MODE == MODE_STEP) {
     {
-      B.hist[idx] = phu;
-      B.hist[P.plane + idx] = phv;
-      B.hist[2 * P.plane + idx] = um;
-      B.hist[3 * P.plane + idx] = cA;
-      B.hist[4 * P.plane + idx] = cB;
+      T* hb = B.hist + ix(P, 5, 0, x, y);
+      hb[0] = phu;
+      hb[pc] = phv;
+      hb[2 * pc] = um;
+      hb[3 * pc] = cA;
+      hb[4 * pc] = cB;
     }
-    if (B.phi_prev) B.phi_prev[idx] = phi;
+    if (B.phi_prev) B.phi_prev[ix(P, 1, 0, x, y)] = phi;
     if (MODE == MODE_HIST) return;
   }
 
@@ -311,17 +317,16 @@ __device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, 
     const T trneq = ((m1 - E1) + T(4) * m0) * T(1.0 / 3.0);
     const T trM2F = (Q1 + T(4) * Q0) * T(1.0 / 3.0);
     const T trS = -s7 * T(1.5) / rho * (trneq + T(0.5) * trM2F);
-    T* M = B.macro;
-    const long long pl = P.plane;
-    M[MAC_PHI * pl + idx] = phi;
-    M[MAC_UX * pl + idx] = u;
-    M[MAC_UY * pl + idx] = v;
-    M[MAC_P * pl + idx] = p;
-    M[MAC_RHO * pl + idx] = rho;
-    M[MAC_MU * pl + idx] = mu;
-    M[MAC_MCX * pl + idx] = mcx;
-    M[MAC_MCY * pl + idx] = mcy;
-    M[MAC_TRS * pl + idx] = trS;
+    T* M = B.macro + ix(P, NMACRO, 0, x, y);
+    M[MAC_PHI * pc] = phi;
+    M[MAC_UX * pc] = u;
+    M[MAC_UY * pc] = v;
+    M[MAC_P * pc] = p;
+    M[MAC_RHO * pc] = rho;
+    M[MAC_MU * pc] = mu;
+    M[MAC_MCX * pc] = mcx;
+    M[MAC_MCY * pc] = mcy;
+    M[MAC_TRS * pc] = trS;
     return;
   }
 
@@ -446,34 +451,29 @@ __device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, 
     gs[7] = b - Xd - Yd + Qq; gs[8] = b + Xd - Yd - Qq;
   }
 
+  T* const fo = B.fout + ix(P, 9, 0, x, y);
+  T* const go = B.gout + ix(P, 9, 0, x, y);
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    B.fout[i * P.plane + idx] = fs[i];
-    B.gout[i * P.plane + idx] = gs[i];
+    fo[i * pc] = fs[i];
+    go[i * pc] = gs[i];
   }
-  if (padL >= 0) {  // periodic copy in the left pad
+  // periodic copies in the row pads (nodes within XPAD of an x edge)
+  if (!P.wall_x && (x < XPAD || x >= P.nx - XPAD)) {
+    const int off = x < XPAD ? P.nx : -P.nx;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      B.fout[i * P.plane + padL] = fs[i];
-      B.gout[i * P.plane + padL] = gs[i];
+      fo[i * pc + off] = fs[i];
+      go[i * pc + off] = gs[i];
     }
-  }
-  if (padR >= 0) {  // periodic copy in the right pad
+    if (x < XPAD && x >= P.nx - XPAD) {  // grids narrower than 2 XPAD: both pads
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      B.fout[i * P.plane + padR] = fs[i];
-      B.gout[i * P.plane + padR] = gs[i];
+      for (int i = 0; i < 9; ++i) {
+        fo[i * pc - P.nx] = fs[i];
+        go[i * pc - P.nx] = gs[i];
+      }
     }
   }
-}
-
-// Pad positions that mirror node (x, y) under a periodic x boundary (-1: none).
-template <typename T>
-__device__ __forceinline__ void pad_slots(const Phys<T>& P, int x, int y, long long& padL, long long& padR) {
-  padL = padR = -1;
-  if (P.wall_x) return;
-  if (x >= P.nx - XPAD) padL = at(P, x - P.nx, y);
-  if (x < XPAD) padR = at(P, x + P.nx, y);
 }
 
 // ---------------------------------------------------------------------------
@@ -634,7 +634,6 @@ __global__ void __launch_bounds__(BX) k_march(const Phys<T> P, const Bufs<T> B) 
     T g[9] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
     T h[5] = {T(0), T(0), T(0), T(0), T(0)};
     T uin = T(0), vin = T(0), pin = T(0);
-    const long long idx = at(P, x, y);
     if (active) {
       if (MODE == MODE_INIT) {
         const long long di = (long long)y * nx + x;
@@ -645,7 +644,7 @@ __global__ void __launch_bounds__(BX) k_march(const Phys<T> P, const Bufs<T> B) 
         pull9(B.gin, P, x, y, g);
         if (MODE == MODE_STEP || MODE == MODE_MACRO) {
 #pragma unroll
-          for (int k = 0; k < 5; ++k) h[k] = B.hist[k * P.plane + idx];
+          for (int k = 0; k < 5; ++k) h[k] = B.hist[ix(P, 5, k, x, y)];
         }
       }
     }
@@ -698,9 +697,7 @@ __global__ void __launch_bounds__(BX) k_march(const Phys<T> P, const Bufs<T> B) 
         mu9[7] = smu[sm][cm - 1];
         mu9[8] = smu[sm][cm + 1];
       }
-      long long padL, padR;
-      pad_slots(P, x, y, padL, padR);
-      node_update<T, MODEL, MODE>(P, B, idx, padL, padR, phi9, mu9, fq[0], g, h, uin, vin, pin);
+      node_update<T, MODEL, MODE>(P, B, x, y, phi9, mu9, fq[0], g, h, uin, vin, pin);
     }
     // advance the queue of pulled f
 #pragma unroll
@@ -725,27 +722,31 @@ __global__ void __launch_bounds__(BX) k_march(const Phys<T> P, const Bufs<T> B) 
 // the failure in *err (the host turns it into LBM_ECUDA), lets the copies it
 // issued land (again with a bound) and returns.
 //
-// Ring depths: f rows y-1 .. y+3 are live while row y is processed (pulls of
-// row y and phi of row y+2), and row y+4 is in flight: 6 slots.  g rows
-// y-1 .. y+1 live, y+2 in flight: 4 slots.
 // ---------------------------------------------------------------------------
-constexpr int SEG = BX + 2 * XPAD;  // staged columns per plane row
-constexpr int RF = 6, RG = 4;
-// Each try_wait suspends for at most ~1 us (the hint), so a wait gives up
-// after about a second; a normal row arrives within microseconds.
-constexpr long long MBAR_SPIN_LIMIT = 1LL << 20;
-constexpr long long MBAR_DRAIN_LIMIT = 1LL << 10;
-
-template <typename T>
+// Staged columns per plane row, for a strip TBX wide.
+template <int TBX>
+struct Seg {
+  static constexpr int value = TBX + 2 * XPAD;
+};
+// Rings: f rows y-1 .. y+3 are live while row y is processed (pulls of row y,
+// phi of row y+2) and DEPTH more rows are in flight; g rows y-1 .. y+1 live
+// plus DEPTH in flight.
+template <typename T, int TBX, int DEPTH>
 struct TmaLayout {
+  static constexpr int SEG = Seg<TBX>::value;
+  static constexpr int RF = 5 + DEPTH, RG = 3 + DEPTH;
   static constexpr size_t f_off = 0;
   static constexpr size_t g_off = f_off + sizeof(T) * RF * 9 * SEG;
   static constexpr size_t phi_off = g_off + sizeof(T) * RG * 9 * SEG;
-  static constexpr size_t bar_off = phi_off + sizeof(T) * RING * (BX + 2);
+  static constexpr size_t bar_off = phi_off + sizeof(T) * RING * (TBX + 2);
   static constexpr size_t bytes = bar_off + 8 * (RF + RG);
   static_assert(g_off % 16 == 0 && phi_off % 16 == 0 && bar_off % 8 == 0, "smem layout alignment");
   static_assert((SEG * sizeof(T)) % 16 == 0, "bulk-copy rows must be 16-byte multiples");
 };
+// Each try_wait suspends for at most ~1 us (the hint), so a wait gives up
+// after about a second; a normal row arrives within microseconds.
+constexpr long long MBAR_SPIN_LIMIT = 1LL << 20;
+constexpr long long MBAR_DRAIN_LIMIT = 1LL << 10;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -798,7 +799,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // Pull of the node in staged column c (row rr) from the source-row slots
 // rm, r0, rp (rows rr-1, rr, rr+1); bounce-back where the source lies beyond
 // a wall.  xg is the node's global column (for the x-wall test).
-template <typename T>
+template <int SEG, typename T>
 __device__ __forceinline__ void pull_staged(const T* rm, const T* r0, const T* rp, int c, bool bxm, bool bxp,
                                             bool bym, bool byp, T out[9]) {
   out[0] = r0[0 * SEG + c];
@@ -812,20 +813,22 @@ __device__ __forceinline__ void pull_staged(const T* rm, const T* r0, const T* r
   out[8] = (bxm || byp) ? r0[6 * SEG + c] : rp[8 * SEG + c - 1];
 }
 
-template <typename T, bool UR>
-__global__ void __launch_bounds__(BX, (sizeof(T) == 4) ? 4 : 2)
+template <typename T, bool UR, int TBX, int DEPTH>
+__global__ void __launch_bounds__(TBX, (sizeof(T) == 4 ? 512 : 256) / TBX)
     k_step_tma(const Phys<T> P, const Bufs<T> B, int* __restrict__ err) {
+  using L = TmaLayout<T, TBX, DEPTH>;
+  constexpr int SEG = L::SEG, RF = L::RF, RG = L::RG;
   extern __shared__ __align__(128) unsigned char smem[];
-  T* const sf = reinterpret_cast<T*>(smem + TmaLayout<T>::f_off);    // [RF][9][SEG]
-  T* const sg = reinterpret_cast<T*>(smem + TmaLayout<T>::g_off);    // [RG][9][SEG]
-  T* const sp = reinterpret_cast<T*>(smem + TmaLayout<T>::phi_off);  // [RING][BX + 2]
-  uint64_t* const barF = reinterpret_cast<uint64_t*>(smem + TmaLayout<T>::bar_off);
+  T* const sf = reinterpret_cast<T*>(smem + L::f_off);    // [RF][9][SEG]
+  T* const sg = reinterpret_cast<T*>(smem + L::g_off);    // [RG][9][SEG]
+  T* const sp = reinterpret_cast<T*>(smem + L::phi_off);  // [RING][TBX + 2]
+  uint64_t* const barF = reinterpret_cast<uint64_t*>(smem + L::bar_off);
   uint64_t* const barG = barF + RF;
 
   const int tid = threadIdx.x;
   const int nx = P.nx, ny = P.ny;
-  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * LY;
-  const int w = min(BX, nx - x0);
+  const int x0 = blockIdx.x * TBX, y0 = blockIdx.y * LY;
+  const int w = min(TBX, nx - x0);
   const int y1 = min(y0 + LY, ny);
   const bool active = tid < w;
   const int x = x0 + tid;
@@ -849,10 +852,10 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4) ? 4 : 2)
       mbar_arrive(bar);
       return;
     }
-    const T* row = src + (long long)wrap_row(r) * P.pitch + x0;  // element x0 - XPAD of the row
+    const T* row = src + (long long)wrap_row(r) * 9 * P.pitch + x0;  // element x0 - XPAD, plane 0
     mbar_arrive_expect_tx(bar, 9u * seg_bytes);
 #pragma unroll 1
-    for (int i = 0; i < 9; ++i) bulk_g2s(slot + i * SEG, row + i * P.plane, seg_bytes, bar);
+    for (int i = 0; i < 9; ++i) bulk_g2s(slot + i * SEG, row + i * P.pitch, seg_bytes, bar);
   };
   auto fslot = [&](int r) { return sf + ((r - fbase) % RF) * (9 * SEG); };
   auto gslot = [&](int r) { return sg + ((r - gbase) % RG) * (9 * SEG); };
@@ -870,28 +873,25 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4) ? 4 : 2)
   // phi of row r (in the domain, or wrapped) into the phi ring: own column,
   // left halo (thread 0), right halo (thread w - 1); x-wall ghosts from the
   // thread's own phi and a second pull of the neighbouring column.
-  auto phi_row = [&](int r) {
+  auto phi_row_at = [&](int r, const T* rm, const T* r0, const T* rp) {
     const int rr = wrap_row(r);
-    const T* rm = fslot(r - 1);
-    const T* r0 = fslot(r);
-    const T* rp = fslot(r + 1);
     const bool bym = wy && rr == 0, byp = wy && rr == ny - 1;
-    T* dst = sp + slot_of(r) * (BX + 2);
+    T* dst = sp + slot_of(r) * (TBX + 2);
     if (!active) return;
     T v[9];
     if (edge_x || bym || byp)
-      pull_staged(rm, r0, rp, tid + XPAD, wx && x == 0, wx && x == nx - 1, bym, byp, v);
+      pull_staged<SEG>(rm, r0, rp, tid + XPAD, wx && x == 0, wx && x == nx - 1, bym, byp, v);
     else
-      pull_staged(rm, r0, rp, tid + XPAD, false, false, false, false, v);
+      pull_staged<SEG>(rm, r0, rp, tid + XPAD, false, false, false, false, v);
     const T ph = sum9(v);
     dst[tid + 1] = ph;
     if (tid == 0) {
       T hv;
       if (x0 > 0 || !wx) {
-        pull_staged(rm, r0, rp, XPAD - 1, false, wx && x0 - 1 == nx - 1, bym, byp, v);
+        pull_staged<SEG>(rm, r0, rp, XPAD - 1, false, wx && x0 - 1 == nx - 1, bym, byp, v);
         hv = sum9(v);
       } else {
-        pull_staged(rm, r0, rp, XPAD + 1, false, wx && 1 == nx - 1, bym, byp, v);
+        pull_staged<SEG>(rm, r0, rp, XPAD + 1, false, wx && 1 == nx - 1, bym, byp, v);
         hv = wall_ghost(P, SIDE_LEFT, ph, sum9(v));
       }
       dst[0] = hv;
@@ -899,27 +899,28 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4) ? 4 : 2)
     if (tid == w - 1) {
       T hv;
       if (x0 + w < nx || !wx) {
-        pull_staged(rm, r0, rp, XPAD + w, wx && x0 + w == 0, wx && x0 + w == nx - 1, bym, byp, v);
+        pull_staged<SEG>(rm, r0, rp, XPAD + w, wx && x0 + w == 0, wx && x0 + w == nx - 1, bym, byp, v);
         hv = sum9(v);
       } else {
-        pull_staged(rm, r0, rp, XPAD + w - 2, wx && nx - 2 == 0, false, bym, byp, v);
+        pull_staged<SEG>(rm, r0, rp, XPAD + w - 2, wx && nx - 2 == 0, false, bym, byp, v);
         hv = wall_ghost(P, SIDE_RIGHT, ph, sum9(v));
       }
       dst[w + 1] = hv;
     }
   };
+  auto phi_row = [&](int r) { phi_row_at(r, fslot(r - 1), fslot(r), fslot(r + 1)); };
   auto ghost_row = [&](int rg, int r1, int r2, int side) {
-    T* d = sp + slot_of(rg) * (BX + 2);
-    const T* a = sp + slot_of(r1) * (BX + 2);
-    const T* b = sp + slot_of(r2) * (BX + 2);
-    for (int j = tid; j < w + 2; j += BX) d[j] = wall_ghost(P, side, a[j], b[j]);
+    T* d = sp + slot_of(rg) * (TBX + 2);
+    const T* a = sp + slot_of(r1) * (TBX + 2);
+    const T* b = sp + slot_of(r2) * (TBX + 2);
+    for (int j = tid; j < w + 2; j += TBX) d[j] = wall_ghost(P, side, a[j], b[j]);
   };
 
   bool ok = true;
   // ---------------------------------------------------------------- prologue
   if (tid == 0) {
-    for (int r = fbase; r <= min(y0 + 3, f_last); ++r) stage_f(r);
-    for (int r = gbase; r <= min(y0 + 1, g_last); ++r) stage_g(r);
+    for (int r = fbase; r <= min(y0 + 2 + DEPTH, f_last); ++r) stage_f(r);
+    for (int r = gbase; r <= min(y0 + DEPTH, g_last); ++r) stage_g(r);
   }
   for (int r = fbase; r <= min(y0 + 2, f_last); ++r) ok = wait_f(r) && ok;
   for (int r = y0 - 1; r <= y0 + 1; ++r)
@@ -932,38 +933,56 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4) ? 4 : 2)
   }
   T h[5] = {T(0), T(0), T(0), T(0), T(0)};
   if (active) {
-    const long long id = at(P, x, y0);
+    const T* hb = B.hist + ix(P, 5, 0, x, y0);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) h[k] = B.hist[k * P.plane + id];
+    for (int k = 0; k < 5; ++k) h[k] = hb[k * P.pitch];
   }
 
   // ---------------------------------------------------------------- march
+  // Ring positions advance by one slot per row: f slot of row y-1 and g slot
+  // of row y-1, and slot + phase parity of the rows waited for (f row y+3,
+  // g row y+1), kept as counters instead of modulo arithmetic.
+  auto next = [](int s, int R) { return s + 1 == R ? 0 : s + 1; };
+  auto add = [](int s, int k, int R) { return s + k >= R ? s + k - R : s + k; };
+  int fA = 1 % RF, gA = 0;                   // rows y0-1 (f: local 1, g: local 0)
+  int fW = 5 % RF, fWp = (5 / RF) & 1;       // f row y0+3 (local 5)
+  int gW = 2 % RG, gWp = (2 / RG) & 1;       // g row y0+1 (local 2)
+  constexpr int FS = 9 * SEG;
   for (int y = y0; y < y1 && !failed; ++y) {
     ok = true;
-    if (y + 3 <= f_last) ok = wait_f(y + 3) && ok;
-    if (y + 1 <= g_last) ok = wait_g(y + 1) && ok;
+    if (y + 3 <= f_last) ok = mbar_wait_bounded(&barF[fW], fWp) && ok;
+    if (y + 1 <= g_last) ok = mbar_wait_bounded(&barG[gW], gWp) && ok;
+    const T* f_m = sf + fA * FS;                 // f row y-1
+    const T* f_0 = sf + add(fA, 1, RF) * FS;     // f row y
+    const T* f_p = sf + add(fA, 2, RF) * FS;     // f row y+1
     const int r2 = y + 2;
     if (r2 <= y1) {
-      if (r2 < ny || !wy) phi_row(r2);
+      if (r2 < ny || !wy) phi_row_at(r2, f_p, sf + add(fA, 3, RF) * FS, sf + add(fA, 4, RF) * FS);
       else if (r2 == ny) ghost_row(ny, ny - 1, ny - 2, SIDE_TOP);  // rows ny-1, ny-2 ready since the last barrier
     }
     failed = __syncthreads_or(!ok);
     if (failed) break;
     if (tid == 0) {
       fence_proxy_async_smem();
-      if (y + 4 <= f_last) stage_f(y + 4);
-      if (y + 2 <= g_last) stage_g(y + 2);
+      if (y + 3 + DEPTH <= f_last) {
+        const int sl = add(fA, 4 + DEPTH, RF);
+        stage(B.fin, sf + sl * FS, &barF[sl], y + 3 + DEPTH);
+      }
+      if (y + 1 + DEPTH <= g_last) {
+        const int sl = add(gA, 2 + DEPTH, RG);
+        stage(B.gin, sg + sl * FS, &barG[sl], y + 1 + DEPTH);
+      }
     }
     T hn[5] = {T(0), T(0), T(0), T(0), T(0)};
     if (active && y + 1 < y1) {
-      const long long id = at(P, x, y + 1);
+      const T* hb = B.hist + ix(P, 5, 0, x, y + 1);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) hn[k] = B.hist[k * P.plane + id];
+      for (int k = 0; k < 5; ++k) hn[k] = hb[k * P.pitch];
     }
     if (active) {
-      const T* pm = sp + slot_of(y - 1) * (BX + 2);
-      const T* p0 = sp + slot_of(y) * (BX + 2);
-      const T* pp = sp + slot_of(y + 1) * (BX + 2);
+      const T* pm = sp + slot_of(y - 1) * (TBX + 2);
+      const T* p0 = sp + slot_of(y) * (TBX + 2);
+      const T* pp = sp + slot_of(y + 1) * (TBX + 2);
       const int c = tid + 1;
       T phi9[9];
       phi9[0] = p0[c];
@@ -975,23 +994,29 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4) ? 4 : 2)
       phi9[6] = pp[c - 1];
       phi9[7] = pm[c - 1];
       phi9[8] = pm[c + 1];
+      const T* g_m = sg + gA * FS;
+      const T* g_0 = sg + add(gA, 1, RG) * FS;
+      const T* g_p = sg + add(gA, 2, RG) * FS;
       const bool bym = wy && y == 0, byp = wy && y == ny - 1;
       T f[9], g[9];
       if (edge_x || bym || byp) {  // bounce-back links possible (block-uniform test)
         const bool bxm = wx && x == 0, bxp = wx && x == nx - 1;
-        pull_staged(fslot(y - 1), fslot(y), fslot(y + 1), tid + XPAD, bxm, bxp, bym, byp, f);
-        pull_staged(gslot(y - 1), gslot(y), gslot(y + 1), tid + XPAD, bxm, bxp, bym, byp, g);
+        pull_staged<SEG>(f_m, f_0, f_p, tid + XPAD, bxm, bxp, bym, byp, f);
+        pull_staged<SEG>(g_m, g_0, g_p, tid + XPAD, bxm, bxp, bym, byp, g);
       } else {
-        pull_staged(fslot(y - 1), fslot(y), fslot(y + 1), tid + XPAD, false, false, false, false, f);
-        pull_staged(gslot(y - 1), gslot(y), gslot(y + 1), tid + XPAD, false, false, false, false, g);
+        pull_staged<SEG>(f_m, f_0, f_p, tid + XPAD, false, false, false, false, f);
+        pull_staged<SEG>(g_m, g_0, g_p, tid + XPAD, false, false, false, false, g);
       }
-      long long padL, padR;
-      pad_slots(P, x, y, padL, padR);
-      node_update<T, MODEL_AC, MODE_STEP, UR>(P, B, at(P, x, y), padL, padR, phi9, phi9, f, g, h, T(0), T(0),
-                                              T(0));
+      node_update<T, MODEL_AC, MODE_STEP, UR>(P, B, x, y, phi9, phi9, f, g, h, T(0), T(0), T(0));
     }
 #pragma unroll
     for (int k = 0; k < 5; ++k) h[k] = hn[k];
+    fA = next(fA, RF);
+    gA = next(gA, RG);
+    fW = next(fW, RF);
+    if (fW == 0) fWp ^= 1;
+    gW = next(gW, RG);
+    if (gW == 0) gWp ^= 1;
   }
   if (failed) {
     // record, then let every copy this block issued land (bounded) before
@@ -1017,9 +1042,9 @@ __global__ void k_pull(const Phys<T> P, const T* __restrict__ in, T* __restrict_
   if (x >= P.nx) return;
   T v[9];
   pull9(in, P, x, y, v);
-  const long long idx = at(P, x, y);
+  T* o = out + ix(P, 9, 0, x, y);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) out[i * P.plane + idx] = v[i];
+  for (int i = 0; i < 9; ++i) o[i * P.pitch] = v[i];
 }
 
 // Inverse of the pull: the population node x sees in direction i came from
@@ -1033,46 +1058,42 @@ __global__ void k_unstream(const Phys<T> P, const T* __restrict__ in, T* __restr
   const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
   const int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
   const int op[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-  const long long idx = at(P, x, y);
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     int sx = x - cx[i], sy = y - cy[i];
     bool wall = false;
     if (sx < 0 || sx >= P.nx) { if (P.wall_x) wall = true; else sx = (sx + P.nx) % P.nx; }
     if (sy < 0 || sy >= P.ny) { if (P.wall_y) wall = true; else sy = (sy + P.ny) % P.ny; }
-    const T val = in[i * P.plane + idx];
+    const T val = in[ix(P, 9, i, x, y)];
     const int dx = wall ? x : sx, dy = wall ? y : sy, di = wall ? op[i] : i;
-    out[di * P.plane + at(P, dx, dy)] = val;
-    long long padL, padR;
-    pad_slots(P, dx, dy, padL, padR);
-    if (padL >= 0) out[di * P.plane + padL] = val;
-    if (padR >= 0) out[di * P.plane + padR] = val;
+    const long long d = ix(P, 9, di, dx, dy);
+    out[d] = val;
+    if (!P.wall_x) {  // periodic copies in the row pads
+      if (dx < XPAD) out[d + P.nx] = val;
+      if (dx >= P.nx - XPAD) out[d - P.nx] = val;
+    }
   }
 }
 
-// pitched T planes -> dense double planes of the region [x0, x0+w) x
-// [y0, y0+hgt) (plane 0 gets + add0)
+// plane k of a set of NP interleaved planes -> dense doubles of the region
+// [x0, x0+w) x [y0, y0+hgt), plus add
 template <typename T>
-__global__ void k_export(const Phys<T> P, const T* __restrict__ in, double* __restrict__ out,
-                         int planes, double add0, int x0, int y0, int w, int hgt) {
+__global__ void k_export(const Phys<T> P, const T* __restrict__ in, int NP, int k, double* __restrict__ out,
+                         double add, int x0, int y0, int w, int hgt) {
   const int xx = blockIdx.x * blockDim.x + threadIdx.x;
   const int yy = blockIdx.y;
   if (xx >= w) return;
-  const long long src = at(P, x0 + xx, y0 + yy);
-  for (int k = 0; k < planes; ++k)
-    out[(long long)k * w * hgt + (long long)yy * w + xx] =
-        double(in[k * P.plane + src]) + (k == 0 ? add0 : 0.0);
+  out[(long long)yy * w + xx] = double(in[ix(P, NP, k, x0 + xx, y0 + yy)]) + add;
 }
 
+// dense doubles (one plane) minus sub -> plane k of a set of NP interleaved planes
 template <typename T>
-__global__ void k_import(const Phys<T> P, const double* __restrict__ in, T* __restrict__ out,
-                         int planes, double sub0) {
+__global__ void k_import(const Phys<T> P, const double* __restrict__ in, T* __restrict__ out, int NP, int k,
+                         double sub) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   if (x >= P.nx) return;
-  for (int k = 0; k < planes; ++k)
-    out[k * P.plane + at(P, x, y)] =
-        T(in[(long long)k * P.nx * P.ny + (long long)y * P.nx + x] - (k == 0 ? sub0 : 0.0));
+  out[ix(P, NP, k, x, y)] = T(in[(long long)y * P.nx + x] - sub);
 }
 
 // Diagnostics, Eqs. (42)-(43), from the MACRO planes and phi(t-1).
@@ -1116,14 +1137,14 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(const Phys<T> P, 
                                                                double* __restrict__ partial) {
   double v[DIAG_FIELDS] = {0, 0, 0, 0, 0, 0};
   const long long N = (long long)P.nx * P.ny;
-  const long long pl = P.plane;
+  const long long pl = P.pitch;  // macro plane k of a node sits k * pitch after plane 0
   const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
   const int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
   const double wi[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
   for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(n / P.nx), x = (int)(n - (long long)y * P.nx);
-    const long long id = at(P, x, y);
+    const long long id = ix(P, NMACRO, 0, x, y);
     const double phi = double(mac[MAC_PHI * pl + id]);
     const double u = double(mac[MAC_UX * pl + id]), vv = double(mac[MAC_UY * pl + id]);
     const double um2 = u * u + vv * vv;
@@ -1141,13 +1162,13 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(const Phys<T> P, 
       int xn = x + cx[k], yn = y + cy[k];
       xn = xn < 0 ? xn + P.nx : (xn >= P.nx ? xn - P.nx : xn);
       yn = yn < 0 ? yn + P.ny : (yn >= P.ny ? yn - P.ny : yn);
-      const long long q = at(P, xn, yn);
+      const long long q = ix(P, NMACRO, 0, xn, yn);
       const double rq = double(mac[MAC_RHO * pl + q]);
       const double Jx = rq * double(mac[MAC_UX * pl + q]) + double(mac[MAC_MCX * pl + q]);
       const double Jy = rq * double(mac[MAC_UY * pl + q]) + double(mac[MAC_MCY * pl + q]);
       div += wi[k] * (cx[k] * Jx + cy[k] * Jy) * 3.0;
     }
-    const double sm = double(P.drho) * (phi - double(phi_prev[id])) + div;
+    const double sm = double(P.drho) * (phi - double(phi_prev[ix(P, 1, 0, x, y)])) + div;
     v[1] += trS * trS;
     v[2] += sm * sm;
     v[5] += 1.0;

@@ -24,21 +24,34 @@ cudaError_t launch_march(int model, int mode, const Phys<T>& P, const Bufs<T>& B
                            : launch_march_model<T, MODEL_AC>(mode, P, B, s);
 }
 
-template <typename T, bool UR>
-static cudaError_t launch_step_tma_ur(const Phys<T>& P, const Bufs<T>& B, int* err, cudaStream_t s) {
+template <typename T, bool UR, int TBX, int DEPTH>
+static cudaError_t launch_tma_variant(const Phys<T>& P, const Bufs<T>& B, int* err, cudaStream_t s) {
+  using L = TmaLayout<T, TBX, DEPTH>;
   // per function and device; cheap next to a step
-  cudaError_t e = cudaFuncSetAttribute(k_step_tma<T, UR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)TmaLayout<T>::bytes);
+  cudaError_t e = cudaFuncSetAttribute(k_step_tma<T, UR, TBX, DEPTH>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (e != cudaSuccess) return e;
-  const dim3 grid((P.nx + BX - 1) / BX, (P.ny + LY - 1) / LY);
-  k_step_tma<T, UR><<<grid, BX, TmaLayout<T>::bytes, s>>>(P, B, err);
+  const dim3 grid((P.nx + TBX - 1) / TBX, (P.ny + LY - 1) / LY);
+  k_step_tma<T, UR, TBX, DEPTH><<<grid, TBX, L::bytes, s>>>(P, B, err);
   return cudaGetLastError();
 }
 
+template <typename T, bool UR>
+static cudaError_t launch_step_tma_ur(const Phys<T>& P, const Bufs<T>& B, int* err, int variant, cudaStream_t s) {
+  switch (variant) {
+    case 1: return launch_tma_variant<T, UR, 256, 1>(P, B, err, s);
+    case 2: return launch_tma_variant<T, UR, 128, 2>(P, B, err, s);
+    case 3: return launch_tma_variant<T, UR, 256, 2>(P, B, err, s);
+    default: return launch_tma_variant<T, UR, 128, 1>(P, B, err, s);
+  }
+}
+
 template <typename T>
-cudaError_t launch_step_tma(const Phys<T>& P, const Bufs<T>& B, int* err, bool unit_rates, cudaStream_t s) {
+cudaError_t launch_step_tma(const Phys<T>& P, const Bufs<T>& B, int* err, bool unit_rates, int variant,
+                            cudaStream_t s) {
   if (P.nx < 4 * XPAD) return cudaErrorNotSupported;
-  return unit_rates ? launch_step_tma_ur<T, true>(P, B, err, s) : launch_step_tma_ur<T, false>(P, B, err, s);
+  return unit_rates ? launch_step_tma_ur<T, true>(P, B, err, variant, s)
+                    : launch_step_tma_ur<T, false>(P, B, err, variant, s);
 }
 
 static inline dim3 row_grid(int nx, int ny, int threads) { return dim3((nx + threads - 1) / threads, ny); }
@@ -56,16 +69,16 @@ cudaError_t launch_unstream(const Phys<T>& P, const T* in, T* out, cudaStream_t 
 }
 
 template <typename T>
-cudaError_t launch_export(const Phys<T>& P, const T* in, double* out, int planes, double add0,
+cudaError_t launch_export(const Phys<T>& P, const T* in, int NP, int k, double* out, double add,
                           int x0, int y0, int w, int hgt, cudaStream_t s) {
-  k_export<T><<<row_grid(w, hgt, 128), 128, 0, s>>>(P, in, out, planes, add0, x0, y0, w, hgt);
+  k_export<T><<<row_grid(w, hgt, 128), 128, 0, s>>>(P, in, NP, k, out, add, x0, y0, w, hgt);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_import(const Phys<T>& P, const double* in, T* out, int planes, double sub0,
+cudaError_t launch_import(const Phys<T>& P, const double* in, T* out, int NP, int k, double sub,
                           cudaStream_t s) {
-  k_import<T><<<row_grid(P.nx, P.ny, 128), 128, 0, s>>>(P, in, out, planes, sub0);
+  k_import<T><<<row_grid(P.nx, P.ny, 128), 128, 0, s>>>(P, in, out, NP, k, sub);
   return cudaGetLastError();
 }
 
@@ -79,12 +92,12 @@ cudaError_t launch_diag(const Phys<T>& P, const T* macro, const T* phi_prev, dou
 
 #define PFLBM_INSTANTIATE(T)                                                                        \
   template cudaError_t launch_march<T>(int, int, const Phys<T>&, const Bufs<T>&, cudaStream_t);   \
-  template cudaError_t launch_step_tma<T>(const Phys<T>&, const Bufs<T>&, int*, bool, cudaStream_t); \
+  template cudaError_t launch_step_tma<T>(const Phys<T>&, const Bufs<T>&, int*, bool, int, cudaStream_t); \
   template cudaError_t launch_pull<T>(const Phys<T>&, const T*, T*, cudaStream_t);                \
   template cudaError_t launch_unstream<T>(const Phys<T>&, const T*, T*, cudaStream_t);            \
-  template cudaError_t launch_export<T>(const Phys<T>&, const T*, double*, int, double, int, int,  \
-                                        int, int, cudaStream_t);                                   \
-  template cudaError_t launch_import<T>(const Phys<T>&, const double*, T*, int, double,           \
+  template cudaError_t launch_export<T>(const Phys<T>&, const T*, int, int, double*, double, int,  \
+                                        int, int, int, cudaStream_t);                              \
+  template cudaError_t launch_import<T>(const Phys<T>&, const double*, T*, int, int, double,      \
                                         cudaStream_t);                                             \
   template cudaError_t launch_diag<T>(const Phys<T>&, const T*, const T*, double*, int, double*,  \
                                       cudaStream_t);
