@@ -38,7 +38,6 @@ struct lbm_handle {
   int* derr = nullptr;  // device flag raised by a kernel whose bounded wait timed out
   bool use_tma = true;
   bool unit_rates = false;  // the rates the paper leaves at 1 are 1
-  int tma_variant = 0;      // strip width / prefetch depth of the TMA step kernel
   int nparts = 0;
   double diag[LBM_NDIAG] = {0};
   int64_t t = 0;
@@ -295,7 +294,7 @@ static int do_step(lbm_handle* h, int64_t n) {
     B.phi_prev = due ? (T*)h->phi_prev : nullptr;
     cudaError_t e = cudaErrorNotSupported;
     if (h->use_tma && h->prm.phase_model == LBM_AC)
-      e = launch_step_tma<T>(P, B, h->derr, h->unit_rates, h->tma_variant, h->stream);
+      e = launch_step_tma<T>(P, B, h->derr, h->unit_rates, h->stream);
     if (e == cudaErrorNotSupported) e = launch_march<T>(h->prm.phase_model, MODE_STEP, P, B, h->stream);
     CUDA_TRY(h, e);
     h->cur ^= 1;
@@ -463,7 +462,6 @@ int lbm_create(const lbm_params* params, void* stream, const lbm_allocator* allo
   }
   h->prec = params->precision;
   h->use_tma = (params->flags & LBM_FLAG_NO_TMA) == 0;
-  if (const char* v = std::getenv("PFLBM_TMA_VARIANT")) h->tma_variant = std::atoi(v);
   h->esize = h->prec == LBM_FP64 ? 8 : 4;
   h->nx = params->nx;
   h->ny = params->ny;

@@ -728,13 +728,13 @@ template <int TBX>
 struct Seg {
   static constexpr int value = TBX + 2 * XPAD;
 };
-// Rings: f rows y-1 .. y+3 are live while row y is processed (pulls of row y,
-// phi of row y+2) and DEPTH more rows are in flight; g rows y-1 .. y+1 live
-// plus DEPTH in flight.
-template <typename T, int TBX, int DEPTH>
+// Rings: f rows y-1 .. y+2 are live while row y is processed (pulls of row y,
+// phi of row y+1) and DF more rows are in flight; g rows y-1 .. y+1 are live
+// and DG more are in flight.
+template <typename T, int TBX, int DF, int DG>
 struct TmaLayout {
   static constexpr int SEG = Seg<TBX>::value;
-  static constexpr int RF = 5 + DEPTH, RG = 3 + DEPTH;
+  static constexpr int RF = 4 + DF, RG = 3 + DG;
   static constexpr size_t f_off = 0;
   static constexpr size_t g_off = f_off + sizeof(T) * RF * 9 * SEG;
   static constexpr size_t phi_off = g_off + sizeof(T) * RG * 9 * SEG;
@@ -813,10 +813,10 @@ __device__ __forceinline__ void pull_staged(const T* rm, const T* r0, const T* r
   out[8] = (bxm || byp) ? r0[6 * SEG + c] : rp[8 * SEG + c - 1];
 }
 
-template <typename T, bool UR, int TBX, int DEPTH>
+template <typename T, bool UR, int TBX, int DF, int DG>
 __global__ void __launch_bounds__(TBX, (sizeof(T) == 4 ? 512 : 256) / TBX)
     k_step_tma(const Phys<T> P, const Bufs<T> B, int* __restrict__ err) {
-  using L = TmaLayout<T, TBX, DEPTH>;
+  using L = TmaLayout<T, TBX, DF, DG>;
   constexpr int SEG = L::SEG, RF = L::RF, RG = L::RG;
   extern __shared__ __align__(128) unsigned char smem[];
   T* const sf = reinterpret_cast<T*>(smem + L::f_off);    // [RF][9][SEG]
@@ -918,17 +918,21 @@ __global__ void __launch_bounds__(TBX, (sizeof(T) == 4 ? 512 : 256) / TBX)
 
   bool ok = true;
   // ---------------------------------------------------------------- prologue
+  // f rows y0-2 .. y0+1+DF and g rows y0-1 .. y0+DG in flight; phi of rows
+  // y0-1 and y0 (and of row 1 when the segment starts at a bottom wall, so
+  // that the ghost row below it can be formed before the march).
+  const bool bottom = wy && y0 == 0;
   if (tid == 0) {
-    for (int r = fbase; r <= min(y0 + 2 + DEPTH, f_last); ++r) stage_f(r);
-    for (int r = gbase; r <= min(y0 + DEPTH, g_last); ++r) stage_g(r);
+    for (int r = fbase; r <= min(y0 + 1 + DF, f_last); ++r) stage_f(r);
+    for (int r = gbase; r <= min(y0 + DG, g_last); ++r) stage_g(r);
   }
-  for (int r = fbase; r <= min(y0 + 2, f_last); ++r) ok = wait_f(r) && ok;
-  for (int r = y0 - 1; r <= y0 + 1; ++r)
-    if (r <= y1 && ((r >= 0 && r < ny) || !wy)) phi_row(r);
+  for (int r = fbase; r <= min(y0 + (bottom ? 2 : 1), f_last); ++r) ok = wait_f(r) && ok;
+  for (int r = gbase; r <= min(y0, g_last); ++r) ok = wait_g(r) && ok;
+  for (int r = y0 - 1; r <= y0 + (bottom ? 1 : 0); ++r)
+    if ((r >= 0 && r < ny) || !wy) phi_row(r);
   bool failed = __syncthreads_or(!ok);
-  if (!failed && wy && (y0 == 0 || y0 + 1 >= ny)) {
-    if (y0 == 0) ghost_row(-1, 0, 1, SIDE_BOTTOM);
-    if (y0 + 1 >= ny) ghost_row(ny, ny - 1, ny - 2, SIDE_TOP);
+  if (!failed && bottom) {
+    ghost_row(-1, 0, 1, SIDE_BOTTOM);
     __syncthreads();
   }
   T h[5] = {T(0), T(0), T(0), T(0), T(0)};
@@ -940,37 +944,36 @@ __global__ void __launch_bounds__(TBX, (sizeof(T) == 4 ? 512 : 256) / TBX)
 
   // ---------------------------------------------------------------- march
   // Ring positions advance by one slot per row: f slot of row y-1 and g slot
-  // of row y-1, and slot + phase parity of the rows waited for (f row y+3,
+  // of row y-1, and slot + phase parity of the rows waited for (f row y+2,
   // g row y+1), kept as counters instead of modulo arithmetic.
   auto next = [](int s, int R) { return s + 1 == R ? 0 : s + 1; };
   auto add = [](int s, int k, int R) { return s + k >= R ? s + k - R : s + k; };
   int fA = 1 % RF, gA = 0;                   // rows y0-1 (f: local 1, g: local 0)
-  int fW = 5 % RF, fWp = (5 / RF) & 1;       // f row y0+3 (local 5)
+  int fW = 4 % RF, fWp = (4 / RF) & 1;       // f row y0+2 (local 4)
   int gW = 2 % RG, gWp = (2 / RG) & 1;       // g row y0+1 (local 2)
   constexpr int FS = 9 * SEG;
   for (int y = y0; y < y1 && !failed; ++y) {
     ok = true;
-    if (y + 3 <= f_last) ok = mbar_wait_bounded(&barF[fW], fWp) && ok;
+    if (y + 2 <= f_last) ok = mbar_wait_bounded(&barF[fW], fWp) && ok;
     if (y + 1 <= g_last) ok = mbar_wait_bounded(&barG[gW], gWp) && ok;
     const T* f_m = sf + fA * FS;                 // f row y-1
     const T* f_0 = sf + add(fA, 1, RF) * FS;     // f row y
     const T* f_p = sf + add(fA, 2, RF) * FS;     // f row y+1
-    const int r2 = y + 2;
-    if (r2 <= y1) {
-      if (r2 < ny || !wy) phi_row_at(r2, f_p, sf + add(fA, 3, RF) * FS, sf + add(fA, 4, RF) * FS);
-      else if (r2 == ny) ghost_row(ny, ny - 1, ny - 2, SIDE_TOP);  // rows ny-1, ny-2 ready since the last barrier
-    }
+    // phi of row y+1 (a ghost row above a top wall)
+    const int r1 = y + 1;
+    if (r1 < ny || !wy) phi_row_at(r1, f_0, f_p, sf + add(fA, 3, RF) * FS);
+    else if (r1 == ny) ghost_row(ny, ny - 1, ny - 2, SIDE_TOP);  // rows ny-1, ny-2 ready since the last barrier
     failed = __syncthreads_or(!ok);
     if (failed) break;
     if (tid == 0) {
       fence_proxy_async_smem();
-      if (y + 3 + DEPTH <= f_last) {
-        const int sl = add(fA, 4 + DEPTH, RF);
-        stage(B.fin, sf + sl * FS, &barF[sl], y + 3 + DEPTH);
+      if (y + 2 + DF <= f_last) {
+        const int sl = add(fA, 3 + DF, RF);
+        stage(B.fin, sf + sl * FS, &barF[sl], y + 2 + DF);
       }
-      if (y + 1 + DEPTH <= g_last) {
-        const int sl = add(gA, 2 + DEPTH, RG);
-        stage(B.gin, sg + sl * FS, &barG[sl], y + 1 + DEPTH);
+      if (y + 1 + DG <= g_last) {
+        const int sl = add(gA, 2 + DG, RG);
+        stage(B.gin, sg + sl * FS, &barG[sl], y + 1 + DG);
       }
     }
     T hn[5] = {T(0), T(0), T(0), T(0), T(0)};

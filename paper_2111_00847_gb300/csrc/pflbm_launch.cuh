@@ -24,34 +24,29 @@ cudaError_t launch_march(int model, int mode, const Phys<T>& P, const Bufs<T>& B
                            : launch_march_model<T, MODEL_AC>(mode, P, B, s);
 }
 
-template <typename T, bool UR, int TBX, int DEPTH>
+template <typename T, bool UR, int TBX, int DF, int DG>
 static cudaError_t launch_tma_variant(const Phys<T>& P, const Bufs<T>& B, int* err, cudaStream_t s) {
-  using L = TmaLayout<T, TBX, DEPTH>;
+  using L = TmaLayout<T, TBX, DF, DG>;
   // per function and device; cheap next to a step
-  cudaError_t e = cudaFuncSetAttribute(k_step_tma<T, UR, TBX, DEPTH>,
+  cudaError_t e = cudaFuncSetAttribute(k_step_tma<T, UR, TBX, DF, DG>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (e != cudaSuccess) return e;
   const dim3 grid((P.nx + TBX - 1) / TBX, (P.ny + LY - 1) / LY);
-  k_step_tma<T, UR, TBX, DEPTH><<<grid, TBX, L::bytes, s>>>(P, B, err);
+  k_step_tma<T, UR, TBX, DF, DG><<<grid, TBX, L::bytes, s>>>(P, B, err);
   return cudaGetLastError();
 }
 
-template <typename T, bool UR>
-static cudaError_t launch_step_tma_ur(const Phys<T>& P, const Bufs<T>& B, int* err, int variant, cudaStream_t s) {
-  switch (variant) {
-    case 1: return launch_tma_variant<T, UR, 256, 1>(P, B, err, s);
-    case 2: return launch_tma_variant<T, UR, 128, 2>(P, B, err, s);
-    case 3: return launch_tma_variant<T, UR, 256, 2>(P, B, err, s);
-    default: return launch_tma_variant<T, UR, 128, 1>(P, B, err, s);
-  }
-}
+// Strip of 128 columns (4 warps); f rows prefetched two march steps ahead,
+// g rows one: 53 KB of shared memory per FP32 block, four blocks per SM.
+// (Deeper prefetch costs a block per SM and measured slower; one-ahead f
+// staging measured the same.)
+constexpr int TMA_TBX = 128, TMA_DF = 2, TMA_DG = 1;
 
 template <typename T>
-cudaError_t launch_step_tma(const Phys<T>& P, const Bufs<T>& B, int* err, bool unit_rates, int variant,
-                            cudaStream_t s) {
+cudaError_t launch_step_tma(const Phys<T>& P, const Bufs<T>& B, int* err, bool unit_rates, cudaStream_t s) {
   if (P.nx < 4 * XPAD) return cudaErrorNotSupported;
-  return unit_rates ? launch_step_tma_ur<T, true>(P, B, err, variant, s)
-                    : launch_step_tma_ur<T, false>(P, B, err, variant, s);
+  return unit_rates ? launch_tma_variant<T, true, TMA_TBX, TMA_DF, TMA_DG>(P, B, err, s)
+                    : launch_tma_variant<T, false, TMA_TBX, TMA_DF, TMA_DG>(P, B, err, s);
 }
 
 static inline dim3 row_grid(int nx, int ny, int threads) { return dim3((nx + threads - 1) / threads, ny); }
@@ -92,7 +87,7 @@ cudaError_t launch_diag(const Phys<T>& P, const T* macro, const T* phi_prev, dou
 
 #define PFLBM_INSTANTIATE(T)                                                                        \
   template cudaError_t launch_march<T>(int, int, const Phys<T>&, const Bufs<T>&, cudaStream_t);   \
-  template cudaError_t launch_step_tma<T>(const Phys<T>&, const Bufs<T>&, int*, bool, int, cudaStream_t); \
+  template cudaError_t launch_step_tma<T>(const Phys<T>&, const Bufs<T>&, int*, bool, cudaStream_t);  \
   template cudaError_t launch_pull<T>(const Phys<T>&, const T*, T*, cudaStream_t);                \
   template cudaError_t launch_unstream<T>(const Phys<T>&, const T*, T*, cudaStream_t);            \
   template cudaError_t launch_export<T>(const Phys<T>&, const T*, int, int, double*, double, int,  \

@@ -14,8 +14,7 @@ cudaError_t launch_march(int model, int mode, const Phys<T>& P, const Bufs<T>& B
 // TMA-staged Allen-Cahn step (returns cudaErrorNotSupported when the grid is
 // too narrow for it; the caller then uses launch_march)
 template <typename T>
-cudaError_t launch_step_tma(const Phys<T>& P, const Bufs<T>& B, int* err, bool unit_rates, int variant,
-                            cudaStream_t s);
+cudaError_t launch_step_tma(const Phys<T>& P, const Bufs<T>& B, int* err, bool unit_rates, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pull(const Phys<T>& P, const T* in, T* out, cudaStream_t s);
 template <typename T>
