@@ -187,6 +187,21 @@ int lbm_fields(lbm_handle *h, int32_t which, double *out);
 int lbm_fields_region(lbm_handle *h, int32_t which, int32_t x0, int32_t y0, int32_t w, int32_t hgt,
                       double *out);
 
+/*
+ * Same result as lbm_fields for LBM_F_POP, LBM_G_POP or LBM_HIST, but with
+ * no device allocation at any point (the paper has no counterpart: this is
+ * a service of the library).  For callers that cannot let the library
+ * allocate: code recording a CUDA stream capture, applications that
+ * reserve all device memory up front, callers whose device is full.
+ * Planes are staged in one fixed 8 MiB array inside the library
+ * (1,048,576 doubles), so grids above 1,048,576 nodes get LBM_EINVAL, as
+ * do other selectors.  The first call on each device looks up that array's
+ * address; make it before any stream capture starts.  The array is shared
+ * by all calls and keeps the last call's contents; calls that run on the GPU
+ * at the same time race on it.  Synchronises the handle's stream.
+ */
+int lbm_fields_noalloc(lbm_handle *h, int32_t which, double *out);
+
 /* Overwrite LBM_F_POP, LBM_G_POP or LBM_HIST (layouts as in lbm_fields) from
  * host doubles, e.g. to resume from a checkpoint.  Other selectors:
  * LBM_EINVAL. */

@@ -32,7 +32,7 @@ LBM_FLAG_NO_TMA = 1
 DIAG_KEYS = ("t", "sum_phi", "Du_rms", "Sm_rms", "umax", "nonfinite", "n_avg", "reserved")
 
 EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_fields", "lbm_fields_region",
-            "lbm_set_fields",
+            "lbm_fields_noalloc", "lbm_set_fields",
             "lbm_time", "lbm_device_bytes", "lbm_destroy", "lbm_last_error")
 
 
@@ -83,6 +83,7 @@ def load(path: str | None = None):
     L.lbm_fields_region.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                     C.c_int32, dp]
     L.lbm_set_fields.argtypes = [C.c_void_p, C.c_int32, dp]
+    L.lbm_fields_noalloc.argtypes = [C.c_void_p, C.c_int32, dp]
     L.lbm_time.argtypes = [C.c_void_p]
     L.lbm_time.restype = C.c_int64
     L.lbm_device_bytes.argtypes = [C.c_void_p]
@@ -159,6 +160,12 @@ def lbm_fields(h, which: int, out: np.ndarray):
 def lbm_fields_region(h, which: int, x0: int, y0: int, w: int, hgt: int, out: np.ndarray):
     _check(load().lbm_fields_region(h, int(which), int(x0), int(y0), int(w), int(hgt),
                                     _dptr(out)), h)
+
+
+def lbm_fields_noalloc(h, which: int, out: np.ndarray):
+    """lbm_fields for LBM_F_POP / LBM_G_POP / LBM_HIST through the library's
+    fixed staging array (no device allocation); grids up to 2^20 nodes."""
+    _check(load().lbm_fields_noalloc(h, int(which), _dptr(out)), h)
 
 
 def lbm_set_fields(h, which: int, arr: np.ndarray):

@@ -546,3 +546,86 @@ void lbm_destroy(lbm_handle* h) {
 const char* lbm_last_error(const lbm_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Population / history export that allocates no device memory.
+//
+// lbm_fields stages each exported plane in a device buffer that the handle
+// creates on first use.  Some callers cannot let the library allocate at
+// that point: code that is recording a CUDA stream capture (cudaMalloc is
+// not permitted there), applications that reserve all device memory up
+// front and forbid later allocations, and callers running with the device
+// already full.  lbm_fields_noalloc exports the same planes through a
+// fixed staging array compiled into the library instead.
+//
+// The array is a file-scope __device__ variable of NOALLOC_MAX_NODES
+// doubles (8 MiB).  Every GPU that loads the library holds it until the
+// process exits.  Host code cannot use the array's name as a device
+// address, so the first call on each device looks the address up with
+// cudaGetSymbolAddress while that device is current.  That first call
+// should therefore come before any stream capture begins.
+//
+// All calls share the one array, and it keeps whatever the last call left
+// in it.  The export overwrites every element it later reads, so nothing
+// needs clearing first.  Calls that run at the same time on the GPU (on
+// different streams or handles) race on the array.
+// ---------------------------------------------------------------------------
+static constexpr long long NOALLOC_MAX_NODES = 1LL << 20;
+static constexpr int NOALLOC_MAX_DEVICES = 64;
+static __device__ __align__(256) double g_noalloc_stage[NOALLOC_MAX_NODES];
+static double* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};  // device address per device ordinal
+
+static int noalloc_stage_for_device(lbm_handle* h, double** out) {
+  int dev = -1;
+  CUDA_TRY(h, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(h, LBM_EINVAL, "device %d out of range", dev);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    CUDA_TRY(h, cudaGetSymbolAddress(&p, g_noalloc_stage));
+    g_noalloc_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return LBM_OK;
+}
+
+template <typename T>
+static int do_fields_noalloc(lbm_handle* h, int which, double* out, double* stage) {
+  const Phys<T> P = make_phys<T>(h);
+  const T* src = nullptr;
+  int NP = 0;
+  double add0 = 0.0;
+  if (which == LBM_F_POP || which == LBM_G_POP) {
+    const int s = which == LBM_F_POP ? 0 : 1;
+    T* spare = (T*)h->pops[s][1 - h->cur];  // allocated by lbm_create
+    CUDA_TRY(h, launch_pull<T>(P, (const T*)h->pops[s][h->cur], spare, h->stream));
+    src = spare;
+    NP = 9;
+    add0 = s == 1 ? h->prm.rho0 : 0.0;
+  } else {
+    src = (const T*)h->hist;
+    NP = 5;
+  }
+  const long long N = (long long)h->nx * h->ny;
+  for (int k = 0; k < NP; ++k) {
+    CUDA_TRY(h, launch_export<T>(P, src, NP, k, stage, k == 0 ? add0 : 0.0, 0, 0, h->nx, h->ny, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(out + k * N, stage, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return check_device_flag(h);
+}
+
+extern "C" int lbm_fields_noalloc(lbm_handle* h, int32_t which, double* out) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!out) return fail(h, LBM_EINVAL, "out is NULL");
+  if (which != LBM_F_POP && which != LBM_G_POP && which != LBM_HIST)
+    return fail(h, LBM_EINVAL, "lbm_fields_noalloc exports only LBM_F_POP, LBM_G_POP and LBM_HIST (got %d)", which);
+  const long long N = (long long)h->nx * h->ny;
+  if (N > NOALLOC_MAX_NODES)
+    return fail(h, LBM_EINVAL, "lbm_fields_noalloc handles at most %lld nodes; this grid has %lld (use lbm_fields)",
+                NOALLOC_MAX_NODES, N);
+  double* stage = nullptr;
+  int rc = noalloc_stage_for_device(h, &stage);
+  if (rc) return rc;
+  return h->prec == LBM_FP64 ? do_fields_noalloc<double>(h, which, out, stage)
+                             : do_fields_noalloc<float>(h, which, out, stage);
+}
