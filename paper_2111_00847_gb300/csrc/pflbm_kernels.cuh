@@ -731,6 +731,11 @@ struct Seg {
 // Rings: f rows y-1 .. y+2 are live while row y is processed (pulls of row y,
 // phi of row y+1) and DF more rows are in flight; g rows y-1 .. y+1 are live
 // and DG more are in flight.
+// phi ring of the TMA step: rows y-2 .. y+1 can be in use at once (slower
+// threads of the previous march step read y-2 .. y while row y+1 is formed)
+constexpr int TRING = 4;
+__host__ __device__ constexpr int tslot(int r) { return (r + 2 * TRING) & (TRING - 1); }
+
 template <typename T, int TBX, int DF, int DG>
 struct TmaLayout {
   static constexpr int SEG = Seg<TBX>::value;
@@ -738,7 +743,7 @@ struct TmaLayout {
   static constexpr size_t f_off = 0;
   static constexpr size_t g_off = f_off + sizeof(T) * RF * 9 * SEG;
   static constexpr size_t phi_off = g_off + sizeof(T) * RG * 9 * SEG;
-  static constexpr size_t bar_off = phi_off + sizeof(T) * RING * (TBX + 2);
+  static constexpr size_t bar_off = phi_off + sizeof(T) * TRING * (TBX + 2);
   static constexpr size_t bytes = bar_off + 8 * (RF + RG);
   static_assert(g_off % 16 == 0 && phi_off % 16 == 0 && bar_off % 8 == 0, "smem layout alignment");
   static_assert((SEG * sizeof(T)) % 16 == 0, "bulk-copy rows must be 16-byte multiples");
@@ -814,14 +819,14 @@ __device__ __forceinline__ void pull_staged(const T* rm, const T* r0, const T* r
 }
 
 template <typename T, bool UR, int TBX, int DF, int DG>
-__global__ void __launch_bounds__(TBX, (sizeof(T) == 4 ? 512 : 256) / TBX)
+__global__ void __launch_bounds__(TBX, (sizeof(T) == 4 ? 640 : 256) / TBX)
     k_step_tma(const Phys<T> P, const Bufs<T> B, int* __restrict__ err) {
   using L = TmaLayout<T, TBX, DF, DG>;
   constexpr int SEG = L::SEG, RF = L::RF, RG = L::RG;
   extern __shared__ __align__(128) unsigned char smem[];
   T* const sf = reinterpret_cast<T*>(smem + L::f_off);    // [RF][9][SEG]
   T* const sg = reinterpret_cast<T*>(smem + L::g_off);    // [RG][9][SEG]
-  T* const sp = reinterpret_cast<T*>(smem + L::phi_off);  // [RING][TBX + 2]
+  T* const sp = reinterpret_cast<T*>(smem + L::phi_off);  // [TRING][TBX + 2]
   uint64_t* const barF = reinterpret_cast<uint64_t*>(smem + L::bar_off);
   uint64_t* const barG = barF + RF;
 
@@ -876,7 +881,7 @@ __global__ void __launch_bounds__(TBX, (sizeof(T) == 4 ? 512 : 256) / TBX)
   auto phi_row_at = [&](int r, const T* rm, const T* r0, const T* rp) {
     const int rr = wrap_row(r);
     const bool bym = wy && rr == 0, byp = wy && rr == ny - 1;
-    T* dst = sp + slot_of(r) * (TBX + 2);
+    T* dst = sp + tslot(r) * (TBX + 2);
     if (!active) return;
     T v[9];
     if (edge_x || bym || byp)
@@ -910,9 +915,9 @@ __global__ void __launch_bounds__(TBX, (sizeof(T) == 4 ? 512 : 256) / TBX)
   };
   auto phi_row = [&](int r) { phi_row_at(r, fslot(r - 1), fslot(r), fslot(r + 1)); };
   auto ghost_row = [&](int rg, int r1, int r2, int side) {
-    T* d = sp + slot_of(rg) * (TBX + 2);
-    const T* a = sp + slot_of(r1) * (TBX + 2);
-    const T* b = sp + slot_of(r2) * (TBX + 2);
+    T* d = sp + tslot(rg) * (TBX + 2);
+    const T* a = sp + tslot(r1) * (TBX + 2);
+    const T* b = sp + tslot(r2) * (TBX + 2);
     for (int j = tid; j < w + 2; j += TBX) d[j] = wall_ghost(P, side, a[j], b[j]);
   };
 
@@ -983,9 +988,9 @@ __global__ void __launch_bounds__(TBX, (sizeof(T) == 4 ? 512 : 256) / TBX)
       for (int k = 0; k < 5; ++k) hn[k] = hb[k * P.pitch];
     }
     if (active) {
-      const T* pm = sp + slot_of(y - 1) * (TBX + 2);
-      const T* p0 = sp + slot_of(y) * (TBX + 2);
-      const T* pp = sp + slot_of(y + 1) * (TBX + 2);
+      const T* pm = sp + tslot(y - 1) * (TBX + 2);
+      const T* p0 = sp + tslot(y) * (TBX + 2);
+      const T* pp = sp + tslot(y + 1) * (TBX + 2);
       const int c = tid + 1;
       T phi9[9];
       phi9[0] = p0[c];

@@ -36,11 +36,13 @@ static cudaError_t launch_tma_variant(const Phys<T>& P, const Bufs<T>& B, int* e
   return cudaGetLastError();
 }
 
-// Strip of 128 columns (4 warps); f rows prefetched two march steps ahead,
-// g rows one: 53 KB of shared memory per FP32 block, four blocks per SM.
-// (Deeper prefetch costs a block per SM and measured slower; one-ahead f
-// staging measured the same.)
-constexpr int TMA_TBX = 128, TMA_DF = 2, TMA_DG = 1;
+// Strip of 160 columns (5 warps), f and g rows staged one march step ahead:
+// 56 KB of shared memory per FP32 block, four blocks (20 warps) per SM.
+// Measured on the 16384^2 FP32 step against the alternatives (GLUPS):
+// 160/1/1 29.5; 128 columns with f two steps ahead (4 blocks) 28.0, with
+// both one ahead (5 blocks) 27.2; 96 columns (6 blocks) 28.2; 192 (3 blocks)
+// 27.6; 256 (2 blocks) 27.5; 160 with f two ahead (3 blocks) 24.9.
+constexpr int TMA_TBX = 160, TMA_DF = 1, TMA_DG = 1;
 
 template <typename T>
 cudaError_t launch_step_tma(const Phys<T>& P, const Bufs<T>& B, int* err, bool unit_rates, cudaStream_t s) {
