@@ -239,3 +239,20 @@ def test_flat_interface_is_stationary(oracle_mod, model):
     assert np.abs(phi - c.phi).max() < 0.02 * dphi
     assert np.abs(o.fields(oracle_mod.UX)).max() < 1e-10
     assert np.abs(o.fields(oracle_mod.UY)).max() < 1e-5
+
+
+def test_diagnostics_vanish_for_fluid_at_rest(oracle_mod):
+    """Eqs. (42)-(43): a uniform fluid at rest has div u = 0 and
+    d rho/dt + div m^CC = 0, so D_u^rms and S_m^rms are zero; Sum phi is the
+    node count times phi."""
+    for walls in ("none", "all"):
+        bc = (0, 0, 0, 0) if walls == "none" else (1, 1, 1, 1)
+        prm = W.Params(nx=20, ny=16, bc=bc, rhoA=5.0, rhoB=1.0, muA=0.5, muB=0.1, diag_every=5)
+        o = oracle_mod.Oracle(prm)
+        o.init_fields(np.full((16, 20), 0.3))
+        o.step(10)
+        d = o.diag()
+        assert d["Du_rms"] < 1e-15 and d["Sm_rms"] < 1e-15, d
+        assert d["umax"] < 1e-15
+        assert d["sum_phi"] == pytest.approx(0.3 * 320, rel=1e-14)
+        assert d["n_avg"] == (320 if walls == "none" else 18 * 14)
