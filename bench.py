@@ -36,7 +36,14 @@ import workloads as W  # noqa: E402
 METRIC = "fused-step MLUPS (phase+flow) and % HBM roofline; adjoint/forward time ratio"
 UNIT = "MLUPS"
 FALLBACK_HBM_GBS = 6800.0
-VALUES_PER_LU = 46  # 18 populations + 5 history values, read and written
+PRECISIONS = {  # name: (lbm precision, dtype label, algorithmic bytes per lattice update)
+    "fp32": (W.PREC_FP32, "f32", 46 * 4),
+    "fp64": (W.PREC_FP64, "f64", 46 * 8),
+    # per set and node: FP32 rest population + 8 x 16-bit deviations (20 B),
+    # two sets read and written, FP32 history read and written
+    "fp16dev": (W.PREC_FP16_DEV, "f32", 2 * 2 * 20 + 2 * 5 * 4),
+    "bf16dev": (W.PREC_BF16_DEV, "f32", 2 * 2 * 20 + 2 * 5 * 4),
+}
 
 
 def parse():
@@ -46,10 +53,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="pflbm", choices=["pflbm", "reference"])
     ap.add_argument("--n", type=int, default=16384, help="grid side")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-storage-compare", action="store_true",
+                    help="skip timing the 16-bit deviation storage beside FP32")
     return ap.parse_args()
 
 
@@ -83,10 +92,10 @@ def measured_peak():
     return FALLBACK_HBM_GBS, "of fallback"
 
 
-def profiled_traffic(esize):
+def profiled_traffic(precision):
     """DRAM bytes per lattice update of the step kernel, from the committed
-    ncu summary (profiles/*.txt line 'dram_bytes_per_lu_fp32: X')."""
-    key = "dram_bytes_per_lu_fp32" if esize == 4 else "dram_bytes_per_lu_fp64"
+    ncu summary (profiles/*.txt line 'dram_bytes_per_lu_<precision>: X')."""
+    key = f"dram_bytes_per_lu_{precision}"
     for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.txt"))):
         for line in open(f):
             m = re.match(rf"\s*{key}\s*:\s*([0-9.eE+-]+)", line)
@@ -228,8 +237,7 @@ def main():
         dist.barrier()
     import paper_2111_00847_gb300 as pk
 
-    prec = W.PREC_FP32 if args.precision == "fp32" else W.PREC_FP64
-    esize = 4 if prec == W.PREC_FP32 else 8
+    prec, dtype, bytes_per_lu = PRECISIONS[args.precision]
     n = args.n
     case = W.rti_multimode(n, precision=prec)
     N = n * n
@@ -246,39 +254,41 @@ def main():
         return float(t.item())
 
     stream = torch.cuda.current_stream(dev)
-    sim = pk.Simulation(case.params, stream=stream)
-    sim.init_fields(case.phi)
-    sim.step(args.warmup)
-    torch.cuda.synchronize()
+    peak, peak_src = measured_peak()
+
+    def timed_steps(params, label, per_lu_bytes):
+        """W warm-up steps, then K steps timed with CUDA events on the
+        simulation's stream (barrier + synchronize on both sides); the
+        roofline of the fused step kernel (one launch per step)."""
+        s = pk.Simulation(params, stream=stream)
+        s.init_fields(case.phi)
+        s.step(args.warmup)
+        torch.cuda.synchronize()
+        clk_s = ClockSampler(local)
+        clk_s.start()
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ck = clk_s.stop()
+        t_ms = max_over_ranks(e0.elapsed_time(e1))
+        launch_s = t_ms / 1e3 / args.steps
+        ach = per_lu_bytes * N / launch_s / 1e9
+        tr, tr_from = profiled_traffic(label)
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": (tr * N if tr is not None else None), "peak_source": peak_src,
+                "algorithmic_bytes_per_lu": per_lu_bytes, "traffic_source": tr_from}
+        return s, t_ms, roof, ck
 
     # ---- device-resident timed region
-    clocks = ClockSampler(local)
-    clocks.start()
-    barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    sim.step(args.steps)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    ms = max_over_ranks(ms)
+    sim, ms, roofline, clk = timed_steps(case.params, args.precision, bytes_per_lu)
     sec = ms / 1e3
     value = world * N * args.steps / sec / 1e6
-    per_launch = sec / args.steps
-
-    # ---- roofline of the dominant kernel (the fused step, one launch per step)
-    peak, peak_src = measured_peak()
-    alg_bytes = VALUES_PER_LU * esize * N
-    achieved = alg_bytes / per_launch / 1e9
-    tr_lu, tr_src = profiled_traffic(esize)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": (tr_lu * N if tr_lu is not None else None),
-                "peak_source": peak_src, "algorithmic_bytes_per_lu": VALUES_PER_LU * esize,
-                "traffic_source": tr_src}
 
     # ---- end to end through the public API, host buffers, copies inside
     e2e = None
@@ -301,6 +311,20 @@ def main():
         del phi_h, out_h
     state_gb = sim.device_bytes / 1e9
     sim.close()
+    del sim
+
+    # ---- the same workload with 16-bit deviation storage (FP32 arithmetic)
+    storage = None
+    if args.precision == "fp32" and not args.no_storage_compare:
+        storage = {}
+        for name in ("fp16dev",):
+            p16, _, b16 = PRECISIONS[name]
+            s16, ms16, roof16, clk16 = timed_steps(case.params.with_(precision=p16), name, b16)
+            s16.close()
+            del s16
+            storage[name] = {"value": world * N * args.steps / (ms16 / 1e3) / 1e6, "unit": UNIT,
+                             "ms_per_step": ms16 / args.steps, "roofline": roof16, "clocks": clk16,
+                             "gain_vs_fp32": ms / ms16}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -309,14 +333,14 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if esize == 4 else "f64",
+                "scaling": "weak", "vs_baseline": None, "dtype": dtype,
                 "data": "synthetic",
                 "config": {"workload": workload_name(n), "nx": n, "ny": n,
                            "precision": args.precision, "phase_model": "AC", "flux": "present",
                            "replicas": world, "parallelism": f"replicas{world}",
                            "l2": f"inputs larger than L2 (device state {state_gb:.1f} GB)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": args.steps, "clocks": clk}
+                "gpu_launches": args.steps, "clocks": clk, "storage_variants": storage}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

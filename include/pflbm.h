@@ -54,7 +54,16 @@ enum {
     LBM_EUNSUPPORTED = -5  /* valid but not implemented in this build */
 };
 
-/* lbm_params.precision: storage and arithmetic type of the populations */
+/* lbm_params.precision: storage and arithmetic type of the populations.
+ *   FP64, FP32: populations, history and arithmetic in that type.
+ *   FP16_DEV, BF16_DEV: FP32 arithmetic and history; per population set and
+ *     node the rest population (f_0, g_0) is stored in FP32 and the eight
+ *     moving ones as 16-bit deviations s (q_i - r_i q_0) from the share the
+ *     node holds at rest (r_i = 9 w_i eta / (9 - 5 eta) for the Allen-Cahn
+ *     f, 0 for the Cahn-Hilliard f, -9 w_i / 5 for g; s a power of two).
+ *     The stored f_0 is solved so that a node's nine decoded f sum to its
+ *     phi, so total phi is conserved independently of the 16-bit rounding.
+ *     An extension beyond the paper, which computes in double precision. */
 enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16_DEV = 2, LBM_BF16_DEV = 3 };
 /* lbm_params.phase_model: D(phi) of Eq. (1) */
 enum { LBM_AC = 0 /* Eq. (7), conservative Allen-Cahn */, LBM_CH = 1 /* Eq. (6), Cahn-Hilliard */ };
@@ -146,9 +155,13 @@ typedef struct lbm_allocator {
  *  stream  cudaStream_t to run on, or NULL
  *  alloc   device-memory provider or NULL
  *  out     receives the handle (NULL on failure)
- * Device memory owned by the handle: 2 x 18 population planes + 5 history
- * planes of the storage type, plus work planes created on first use by
- * lbm_fields / diagnostics.  All of it is released by lbm_destroy.
+ * Device memory owned by the handle: 2 x 18 population planes (16-bit
+ * deviation storage: 2 x 2 FP32 + 2 x 16 16-bit planes), 5 history planes
+ * and one phi plane of the arithmetic type, plus work planes created on
+ * first use by lbm_fields / diagnostics.  With 16-bit storage,
+ * lbm_init_fields and lbm_set_fields of populations also hold 9 (18 for
+ * init) FP32 scratch planes for the duration of the call.  All of it is
+ * released by lbm_destroy.
  */
 int lbm_create(const lbm_params *params, void *stream, const lbm_allocator *alloc,
                lbm_handle **out);

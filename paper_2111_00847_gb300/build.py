@@ -1,7 +1,8 @@
 """In-tree build of the CUDA library ``libpflbm.so`` for sm_103a.
 
-Three translation units (the C-ABI host code and the FP32 / FP64 device
-instantiations) are compiled in parallel with nvcc and linked into one shared
+Five translation units (the C-ABI host code and the device instantiations
+for FP64, FP32, FP16-deviation and BF16-deviation storage) are compiled in
+parallel with nvcc and linked into one shared
 object beside this file.  The CUDA runtime is linked statically, so the
 library needs only the driver at run time.
 """
@@ -17,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpflbm.so")
-SOURCES = ["pflbm_capi.cu", "pflbm_f32.cu", "pflbm_f64.cu"]
+SOURCES = ["pflbm_capi.cu", "pflbm_f32.cu", "pflbm_f64.cu", "pflbm_f16.cu", "pflbm_bf16.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xptxas", "-v"]

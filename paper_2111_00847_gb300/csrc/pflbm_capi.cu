@@ -4,6 +4,7 @@
 // caller-supplied allocator), the per-run constants handed to the kernels,
 // and the sequencing of launches on the handle's stream.  Every step of the
 // method runs in the device kernels of pflbm_kernels.cuh.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -23,7 +24,8 @@ struct lbm_handle {
   lbm_allocator alloc{};
   bool have_alloc = false;
   int prec = LBM_FP64;
-  size_t esize = 8;
+  size_t esize = 8;      // bytes of the arithmetic type (history, macro planes)
+  long long pop_bytes = 0;  // bytes of one population set (codec layout)
   int nx = 0, ny = 0, pitch = 0;
   long long plane = 0;
   void* pops[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [f|g][A|B]
@@ -48,6 +50,7 @@ struct lbm_handle {
   double beta, kappa, lam_coef, drho, sf[9], sg[9], H;
   bool sg_node[9];
   double wa[4];
+  double dv_r[2][2], dv_s[2], dv_c0;  // 16-bit deviation storage constants
 };
 
 static std::string g_create_error;
@@ -105,12 +108,12 @@ static int validate(const lbm_params* P) {
   if (!P) return fail(nullptr, LBM_EINVAL, "params is NULL");
   if (P->version != LBM_ABI_VERSION) return fail(nullptr, LBM_EINVAL, "params.version %d != %d", P->version, LBM_ABI_VERSION);
   if (P->nx < 3 || P->ny < 3) return fail(nullptr, LBM_EINVAL, "grid %d x %d: each side must be >= 3", P->nx, P->ny);
-  const long long pitch = ((long long)P->nx + 2 * XPAD + 4 + 31) / 32 * 32;
+  const long long pitch = ((long long)P->nx + 2 * XPAD + 8 + 31) / 32 * 32;
   if (P->ny > 65535) return fail(nullptr, LBM_EINVAL, "ny = %d exceeds 65535", P->ny);
   if (pitch * P->ny >= (1LL << 31)) return fail(nullptr, LBM_EINVAL, "grid %d x %d too large (pitch*ny must be < 2^31)", P->nx, P->ny);
-  if (P->precision == LBM_FP16_DEV || P->precision == LBM_BF16_DEV)
-    return fail(nullptr, LBM_EUNSUPPORTED, "reduced-precision storage is not built in this library");
-  if (P->precision != LBM_FP64 && P->precision != LBM_FP32) return fail(nullptr, LBM_EINVAL, "precision %d", P->precision);
+  if (P->precision != LBM_FP64 && P->precision != LBM_FP32 && P->precision != LBM_FP16_DEV &&
+      P->precision != LBM_BF16_DEV)
+    return fail(nullptr, LBM_EINVAL, "precision %d", P->precision);
   if (P->phase_model != LBM_AC && P->phase_model != LBM_CH) return fail(nullptr, LBM_EINVAL, "phase_model %d", P->phase_model);
   if (P->flux_model == LBM_CORRECTED) return fail(nullptr, LBM_EUNSUPPORTED, "flux_model CORRECTED is not built in this library");
   if (P->flux_model != LBM_PRESENT && P->flux_model != LBM_ORIGINAL) return fail(nullptr, LBM_EINVAL, "flux_model %d", P->flux_model);
@@ -157,6 +160,26 @@ static void derive(lbm_handle* h) {
   // App. C: H = (s_g^2 - s_g^0) / (9 s_g^0 s_g^2)
   h->H = (h->sg[2] - h->sg[0]) / (9.0 * h->sg[0] * h->sg[2]);
   for (int s = 0; s < 4; ++s) h->wa[s] = 4.0 * cos_deg(P.theta_deg[s]) / (P.width * dphi);
+  // 16-bit deviation storage.  r: the ratios f_i / f_0 of a node at rest.
+  // Allen-Cahn f^eq at u = 0 (Eq. (C.4)): f_0 = (1 - 5 eta / 9) phi, f_i =
+  // w_i eta phi, so r_i = 9 w_i eta / (9 - 5 eta) (while f_0 keeps at least a
+  // quarter of phi; else no reference).  Cahn-Hilliard f^eq at rest moves
+  // only eta mu_phi (Eq. (C.3)), which vanishes in the bulk: r = 0.  g^eq at
+  // rest (Eq. (C.2), g_0 stored minus rho0): g_0 = -(5/3) p, g_i = 3 w_i p,
+  // so r_i = -9 w_i / 5.  Scales: 2^13 over the largest |phi| (rho) rounded
+  // up to a power of two keeps FP16 deviations far below its 65504 limit
+  // and above its subnormal range; BF16 has the FP32 exponent range.
+  const bool ac_ref = P.phase_model == LBM_AC && 9.0 - 5.0 * P.eta >= 2.25;
+  h->dv_r[0][0] = ac_ref ? P.eta / (9.0 - 5.0 * P.eta) : 0.0;
+  h->dv_r[0][1] = ac_ref ? 0.25 * P.eta / (9.0 - 5.0 * P.eta) : 0.0;
+  h->dv_c0 = 1.0 / (1.0 + 4.0 * h->dv_r[0][0] + 4.0 * h->dv_r[0][1]);
+  h->dv_r[1][0] = -1.0 / 5.0;
+  h->dv_r[1][1] = -1.0 / 20.0;
+  const double phimax = std::max(std::fabs(P.phiA), std::fabs(P.phiB));
+  const double rhomax = std::max(P.rhoA, P.rhoB);
+  const bool half = P.precision == LBM_FP16_DEV;
+  h->dv_s[0] = half ? std::ldexp(1.0, 13 - (int)std::ceil(std::log2(phimax))) : 1.0;
+  h->dv_s[1] = half ? std::ldexp(1.0, 13 - (int)std::ceil(std::log2(rhomax))) : 1.0;
 }
 
 template <typename T>
@@ -202,6 +225,13 @@ static Phys<T> make_phys(const lbm_handle* h) {
     P.hg[k] = T(1.0 - 0.5 * h->sg[k]);
   }
   for (int s = 0; s < 4; ++s) P.wa[s] = T(h->wa[s]);
+  for (int set = 0; set < 2; ++set) {
+    P.dv_r[set][0] = T(h->dv_r[set][0]);
+    P.dv_r[set][1] = T(h->dv_r[set][1]);
+    P.dv_s[set] = T(h->dv_s[set]);
+    P.dv_is[set] = T(1.0 / h->dv_s[set]);
+  }
+  P.dv_c0 = T(h->dv_c0);
   return P;
 }
 
@@ -212,10 +242,10 @@ template <typename T>
 static Bufs<T> bufs_now(lbm_handle* h) {
   Bufs<T> B;
   std::memset(&B, 0, sizeof(B));
-  B.fin = (const T*)h->pops[0][h->cur];
-  B.gin = (const T*)h->pops[1][h->cur];
-  B.fout = (T*)h->pops[0][1 - h->cur];
-  B.gout = (T*)h->pops[1][1 - h->cur];
+  B.fin = h->pops[0][h->cur];
+  B.gin = h->pops[1][h->cur];
+  B.fout = h->pops[0][1 - h->cur];
+  B.gout = h->pops[1][1 - h->cur];
   B.hist = (T*)h->hist;
   B.macro = (T*)h->macro;
   return B;
@@ -250,20 +280,22 @@ static int check_device_flag(lbm_handle* h) {
   return LBM_OK;
 }
 
-template <typename T>
+template <class C>
 static int run_macro(lbm_handle* h) {
+  using T = typename C::value_t;
   int rc = ensure_macro(h);
   if (rc) return rc;
   const Phys<T> P = make_phys<T>(h);
   Bufs<T> B = bufs_now<T>(h);
   B.macro = (T*)h->macro;
-  CUDA_TRY(h, launch_march<T>(h->prm.phase_model, MODE_MACRO, P, B, h->stream));
+  CUDA_TRY(h, launch_march<C>(h->prm.phase_model, MODE_MACRO, P, B, h->stream));
   return LBM_OK;
 }
 
-template <typename T>
+template <class C>
 static int run_diag(lbm_handle* h) {
-  int rc = run_macro<T>(h);
+  using T = typename C::value_t;
+  int rc = run_macro<C>(h);
   if (rc) return rc;
   const Phys<T> P = make_phys<T>(h);
   CUDA_TRY(h, launch_diag<T>(P, (const T*)h->macro, (const T*)h->phi_prev, h->dpart, h->nparts, h->ddiag, h->stream));
@@ -284,8 +316,9 @@ static int run_diag(lbm_handle* h) {
   return LBM_OK;
 }
 
-template <typename T>
+template <class C>
 static int do_step(lbm_handle* h, int64_t n) {
+  using T = typename C::value_t;
   const Phys<T> P = make_phys<T>(h);
   const int de = h->prm.diag_every;
   for (int64_t s = 0; s < n; ++s) {
@@ -294,13 +327,13 @@ static int do_step(lbm_handle* h, int64_t n) {
     B.phi_prev = due ? (T*)h->phi_prev : nullptr;
     cudaError_t e = cudaErrorNotSupported;
     if (h->use_tma && h->prm.phase_model == LBM_AC)
-      e = launch_step_tma<T>(P, B, h->derr, h->unit_rates, h->stream);
-    if (e == cudaErrorNotSupported) e = launch_march<T>(h->prm.phase_model, MODE_STEP, P, B, h->stream);
+      e = launch_step_tma<C>(P, B, h->derr, h->unit_rates, h->stream);
+    if (e == cudaErrorNotSupported) e = launch_march<C>(h->prm.phase_model, MODE_STEP, P, B, h->stream);
     CUDA_TRY(h, e);
     h->cur ^= 1;
     h->t += 1;
     if (due) {
-      int rc = run_diag<T>(h);
+      int rc = run_diag<C>(h);
       if (rc) return rc;
       if (h->diag[5] > 0 || !(h->diag[4] <= 0.4))
         return fail(h, LBM_EUNSTABLE, "unstable at t=%lld: %g non-finite nodes, max|u| = %g",
@@ -311,8 +344,18 @@ static int do_step(lbm_handle* h, int64_t n) {
   return LBM_OK;
 }
 
+// Plain arithmetic-type scratch of nine planes (deviation storage: the
+// pulled-layout equilibria and imported populations before encoding).
+// Allocated per use and released by the caller, so that a run with 16-bit
+// storage keeps its smaller footprint between such calls.
 template <typename T>
+static T* alloc_plain_pops(lbm_handle* h, int sets) {
+  return (T*)dev_alloc(h, (size_t)sets * 9 * h->plane * sizeof(T));
+}
+
+template <class C>
 static int do_init(lbm_handle* h, const double* phi, const double* ux, const double* uy, const double* p) {
+  using T = typename C::value_t;
   const long long N = (long long)h->nx * h->ny;
   const int planes = 1 + (ux ? 1 : 0) + (uy ? 1 : 0) + (p ? 1 : 0);
   int rc = ensure_stage(h, planes);
@@ -326,14 +369,29 @@ static int do_init(lbm_handle* h, const double* phi, const double* ux, const dou
   if (ux) { CUDA_TRY(h, cudaMemcpyAsync(d, ux, N * sizeof(double), cudaMemcpyHostToDevice, h->stream)); B.iux = d; d += N; }
   if (uy) { CUDA_TRY(h, cudaMemcpyAsync(d, uy, N * sizeof(double), cudaMemcpyHostToDevice, h->stream)); B.iuy = d; d += N; }
   if (p) { CUDA_TRY(h, cudaMemcpyAsync(d, p, N * sizeof(double), cudaMemcpyHostToDevice, h->stream)); B.ip = d; d += N; }
-  // equilibria per node into the spare buffers, then scatter to the pull layout
-  CUDA_TRY(h, launch_march<T>(h->prm.phase_model, MODE_INIT, P, B, h->stream));
-  CUDA_TRY(h, launch_unstream<T>(P, (const T*)h->pops[0][1 - h->cur], (T*)h->pops[0][h->cur], h->stream));
-  CUDA_TRY(h, launch_unstream<T>(P, (const T*)h->pops[1][1 - h->cur], (T*)h->pops[1][h->cur], h->stream));
+  if constexpr (!C::dev) {
+    // equilibria per node into the spare buffers, then scatter to the pull layout
+    CUDA_TRY(h, launch_march<C>(h->prm.phase_model, MODE_INIT, P, B, h->stream));
+    CUDA_TRY(h, launch_unstream<T>(P, (const T*)h->pops[0][1 - h->cur], (T*)h->pops[0][h->cur], h->stream));
+    CUDA_TRY(h, launch_unstream<T>(P, (const T*)h->pops[1][1 - h->cur], (T*)h->pops[1][h->cur], h->stream));
+  } else {
+    // equilibria per node into plain scratch, then encode node by node
+    T* scratch = alloc_plain_pops<T>(h, 2);
+    if (!scratch) return fail(h, LBM_ENOMEM, "scratch for the initial populations");
+    T* gs = scratch + 9 * h->plane;
+    B.fout = scratch;
+    B.gout = gs;
+    cudaError_t e = launch_march<C>(h->prm.phase_model, MODE_INIT, P, B, h->stream);
+    if (e == cudaSuccess) e = launch_restream<C>(P, scratch, h->pops[0][h->cur], 0, h->stream);
+    if (e == cudaSuccess) e = launch_restream<C>(P, gs, h->pops[1][h->cur], 1, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    dev_free(h, scratch);
+    CUDA_TRY(h, e);
+  }
   // history := chi(0), and phi(t-1) := phi(0)
   Bufs<T> Bh = bufs_now<T>(h);
   Bh.phi_prev = (T*)h->phi_prev;
-  CUDA_TRY(h, launch_march<T>(h->prm.phase_model, MODE_HIST, P, Bh, h->stream));
+  CUDA_TRY(h, launch_march<C>(h->prm.phase_model, MODE_HIST, P, Bh, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   h->t = 0;
   std::memset(h->diag, 0, sizeof(h->diag));
@@ -376,13 +434,35 @@ static int import_planes(lbm_handle* h, const double* in, int NP, double sub0, T
   return LBM_OK;
 }
 
-template <typename T>
+// deviation storage: pulled populations of a region, decoded, -> host
+template <class C>
+static int export_pulled(lbm_handle* h, int set, double* out, Region r, double* stage) {
+  using T = typename C::value_t;
+  const Phys<T> P = make_phys<T>(h);
+  const long long N = (long long)r.w * r.h;
+  for (int k = 0; k < 9; ++k) {
+    CUDA_TRY(h, launch_pull_export<C>(P, h->pops[set][h->cur], set, k, stage,
+                                      (k == 0 && set == 1) ? h->prm.rho0 : 0.0, r.x0, r.y0, r.w, r.h,
+                                      h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(out + k * N, stage, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return check_device_flag(h);
+}
+
+template <class C>
 static int do_fields(lbm_handle* h, int which, double* out, Region reg) {
+  using T = typename C::value_t;
   const Phys<T> P = make_phys<T>(h);
   switch (which) {
     case LBM_F_POP:
     case LBM_G_POP: {
       const int s = which == LBM_F_POP ? 0 : 1;
+      if constexpr (C::dev) {
+        int rc = ensure_stage(h, 1);
+        if (rc) return rc;
+        return export_pulled<C>(h, s, out, reg, h->dstage);
+      }
       T* scratch = (T*)h->pops[s][1 - h->cur];
       CUDA_TRY(h, launch_pull<T>(P, (const T*)h->pops[s][h->cur], scratch, h->stream));
       return export_planes<T>(h, scratch, 9, 0, 9, s == 1 ? h->prm.rho0 : 0.0, out, reg);
@@ -390,7 +470,7 @@ static int do_fields(lbm_handle* h, int which, double* out, Region reg) {
     case LBM_HIST:
       return export_planes<T>(h, (const T*)h->hist, 5, 0, 5, 0.0, out, reg);
     case LBM_DIAG: {
-      int rc = run_diag<T>(h);
+      int rc = run_diag<C>(h);
       if (rc) return rc;
       std::memcpy(out, h->diag, sizeof(h->diag));
       return LBM_OK;
@@ -410,18 +490,31 @@ static int do_fields(lbm_handle* h, int which, double* out, Region reg) {
     case LBM_MCY: plane = MAC_MCY; break;
     default: return fail(h, LBM_EINVAL, "unknown field selector %d", which);
   }
-  int rc = run_macro<T>(h);
+  int rc = run_macro<C>(h);
   if (rc) return rc;
   return export_planes<T>(h, (const T*)h->macro, NMACRO, plane, 1, 0.0, out, reg);
 }
 
-template <typename T>
+template <class C>
 static int do_set_fields(lbm_handle* h, int which, const double* in) {
+  using T = typename C::value_t;
   const Phys<T> P = make_phys<T>(h);
   switch (which) {
     case LBM_F_POP:
     case LBM_G_POP: {
       const int s = which == LBM_F_POP ? 0 : 1;
+      if constexpr (C::dev) {
+        T* scratch = alloc_plain_pops<T>(h, 1);
+        if (!scratch) return fail(h, LBM_ENOMEM, "scratch for the imported populations");
+        int rc = import_planes<T>(h, in, 9, s == 1 ? h->prm.rho0 : 0.0, scratch);
+        cudaError_t e = cudaSuccess;
+        if (!rc) e = launch_restream<C>(P, scratch, h->pops[s][h->cur], s, h->stream);
+        if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        dev_free(h, scratch);
+        if (rc) return rc;
+        CUDA_TRY(h, e);
+        return LBM_OK;
+      }
       T* scratch = (T*)h->pops[s][1 - h->cur];
       int rc = import_planes<T>(h, in, 9, s == 1 ? h->prm.rho0 : 0.0, scratch);
       if (rc) return rc;
@@ -435,6 +528,15 @@ static int do_set_fields(lbm_handle* h, int which, const double* in) {
       return fail(h, LBM_EINVAL, "field %d cannot be set", which);
   }
 }
+
+// Run the codec-templated operation that matches the handle's storage.
+#define PFLBM_DISPATCH(h, fn, ...)                                         \
+  switch ((h)->prec) {                                                     \
+    case LBM_FP64: return fn<PopPlain<double>>(__VA_ARGS__);               \
+    case LBM_FP32: return fn<PopPlain<float>>(__VA_ARGS__);                \
+    case LBM_FP16_DEV: return fn<PopDev<__half>>(__VA_ARGS__);             \
+    default: return fn<PopDev<__nv_bfloat16>>(__VA_ARGS__);                \
+  }
 
 // ---------------------------------------------------------------------------
 // C entry points
@@ -462,18 +564,21 @@ int lbm_create(const lbm_params* params, void* stream, const lbm_allocator* allo
   }
   h->prec = params->precision;
   h->use_tma = (params->flags & LBM_FLAG_NO_TMA) == 0;
+  const bool dev16 = h->prec == LBM_FP16_DEV || h->prec == LBM_BF16_DEV;
   h->esize = h->prec == LBM_FP64 ? 8 : 4;
   h->nx = params->nx;
   h->ny = params->ny;
   // rows carry XPAD pad elements per side; the pitch leaves room for a
-  // 16-byte rounded bulk copy of the last strip's segment
-  h->pitch = (h->nx + 2 * XPAD + 4 + 31) / 32 * 32;
+  // 16-byte rounded bulk copy of the last strip's segment (up to 7 more
+  // elements for 2-byte planes, 3 for 4-byte ones)
+  h->pitch = (h->nx + 2 * XPAD + (dev16 ? 8 : 4) + 31) / 32 * 32;
   h->plane = (long long)h->pitch * h->ny;
   derive(h);
   const size_t pl = (size_t)h->plane * h->esize;
+  h->pop_bytes = (dev16 ? pop_row_bytes<PopDev<__half>>(h->pitch) : 9LL * h->pitch * (long long)h->esize) * h->ny;
   bool ok = true;
   for (int s = 0; s < 2; ++s)
-    for (int b = 0; b < 2; ++b) ok = ok && (h->pops[s][b] = dev_alloc(h, 9 * pl));
+    for (int b = 0; b < 2; ++b) ok = ok && (h->pops[s][b] = dev_alloc(h, (size_t)h->pop_bytes));
   ok = ok && (h->hist = dev_alloc(h, 5 * pl));
   ok = ok && (h->phi_prev = dev_alloc(h, pl));
   const long long N = (long long)h->nx * h->ny;
@@ -500,13 +605,13 @@ int lbm_create(const lbm_params* params, void* stream, const lbm_allocator* allo
 int lbm_init_fields(lbm_handle* h, const double* phi, const double* ux, const double* uy, const double* p) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   if (!phi) return fail(h, LBM_EINVAL, "phi is NULL");
-  return h->prec == LBM_FP64 ? do_init<double>(h, phi, ux, uy, p) : do_init<float>(h, phi, ux, uy, p);
+  PFLBM_DISPATCH(h, do_init, h, phi, ux, uy, p);
 }
 
 int lbm_step(lbm_handle* h, int64_t nsteps) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps < 0");
-  return h->prec == LBM_FP64 ? do_step<double>(h, nsteps) : do_step<float>(h, nsteps);
+  PFLBM_DISPATCH(h, do_step, h, nsteps);
 }
 
 int lbm_fields_region(lbm_handle* h, int32_t which, int32_t x0, int32_t y0, int32_t w, int32_t hgt,
@@ -517,7 +622,7 @@ int lbm_fields_region(lbm_handle* h, int32_t which, int32_t x0, int32_t y0, int3
     return fail(h, LBM_EINVAL, "region [%d,%d)x[%d,%d) outside the %d x %d grid", x0, x0 + w, y0, y0 + hgt,
                 h->nx, h->ny);
   const Region r{x0, y0, w, hgt};
-  return h->prec == LBM_FP64 ? do_fields<double>(h, which, out, r) : do_fields<float>(h, which, out, r);
+  PFLBM_DISPATCH(h, do_fields, h, which, out, r);
 }
 
 int lbm_fields(lbm_handle* h, int32_t which, double* out) {
@@ -528,7 +633,7 @@ int lbm_fields(lbm_handle* h, int32_t which, double* out) {
 int lbm_set_fields(lbm_handle* h, int32_t which, const double* in) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   if (!in) return fail(h, LBM_EINVAL, "in is NULL");
-  return h->prec == LBM_FP64 ? do_set_fields<double>(h, which, in) : do_set_fields<float>(h, which, in);
+  PFLBM_DISPATCH(h, do_set_fields, h, which, in);
 }
 
 int64_t lbm_time(const lbm_handle* h) { return h ? h->t : -1; }
@@ -588,12 +693,17 @@ static int noalloc_stage_for_device(lbm_handle* h, double** out) {
   return LBM_OK;
 }
 
-template <typename T>
+template <class C>
 static int do_fields_noalloc(lbm_handle* h, int which, double* out, double* stage) {
+  using T = typename C::value_t;
   const Phys<T> P = make_phys<T>(h);
   const T* src = nullptr;
   int NP = 0;
   double add0 = 0.0;
+  if constexpr (C::dev) {  // decoded straight into the staging array
+    if (which == LBM_F_POP || which == LBM_G_POP)
+      return export_pulled<C>(h, which == LBM_F_POP ? 0 : 1, out, Region{0, 0, h->nx, h->ny}, stage);
+  }
   if (which == LBM_F_POP || which == LBM_G_POP) {
     const int s = which == LBM_F_POP ? 0 : 1;
     T* spare = (T*)h->pops[s][1 - h->cur];  // allocated by lbm_create
@@ -626,6 +736,5 @@ extern "C" int lbm_fields_noalloc(lbm_handle* h, int32_t which, double* out) {
   double* stage = nullptr;
   int rc = noalloc_stage_for_device(h, &stage);
   if (rc) return rc;
-  return h->prec == LBM_FP64 ? do_fields_noalloc<double>(h, which, out, stage)
-                             : do_fields_noalloc<float>(h, which, out, stage);
+  PFLBM_DISPATCH(h, do_fields_noalloc, h, which, out, stage);
 }

@@ -1,0 +1,6 @@
+// FP16-deviation storage instantiation of the device path (FP32 arithmetic).
+#include "pflbm_launch.cuh"
+
+namespace pflbm {
+PFLBM_INSTANTIATE_DEV(PopDev<__half>)
+}  // namespace pflbm

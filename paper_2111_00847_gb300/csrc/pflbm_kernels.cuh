@@ -35,8 +35,12 @@
 // node and no dense contraction.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 namespace pflbm {
 
@@ -80,14 +84,62 @@ struct Phys {
   T sf[9], hf[9];            // s_f^k and 1 - s_f^k / 2
   T sg[9], hg[9];
   T wa[4];                   // a = 4 cos(theta) / (W dphi) per side, Eq. (50)
+  // 16-bit deviation storage (PopDev): per population set (0 = f, 1 = g)
+  // the reference ratios r (axis, diagonal directions), the power-of-two
+  // scale s of the stored deviations and 1/s, and for f the factor
+  // 1 / (1 + sum_i r_i) that makes a node's decoded populations sum to phi.
+  T dv_r[2][2], dv_s[2], dv_is[2], dv_c0;
 };
+
+// Population sets are addressed in bytes through a storage codec: plane 0
+// of a row block holds B0-byte elements, planes 1..8 BI-byte elements, and
+// a row block is pitch (B0 + 8 BI) bytes.  PopPlain stores every population
+// in the arithmetic type (the layout in the file header).  PopDev<Q> stores
+// the rest population f_0 (g_0) of a node in FP32 and the eight moving ones
+// as Q (FP16 or BF16) deviations from r_i times it:
+//   q_i = Q( s (f_i - r_i f_0) ),   decoded  f_i = q_i / s + r_i f_0,
+// where r_i is the ratio f_i / f_0 of the node at rest, so that q_i carries
+// only the velocity and non-equilibrium part.  For f the stored f_0 is then
+// re-solved from the rounded q_i so that the decoded nine sum to phi
+// exactly (conservation of phi does not depend on the 16-bit rounding).
+template <typename T>
+struct PopPlain {
+  using value_t = T;
+  using raw_t = T;
+  static constexpr bool dev = false;
+  static constexpr int B0 = sizeof(T), BI = sizeof(T);
+};
+template <typename Q>
+struct PopDev {
+  using value_t = float;
+  using raw_t = Q;
+  static constexpr bool dev = true;
+  static constexpr int B0 = 4, BI = 2;
+};
+template <class C>
+__host__ __device__ constexpr long long pop_row_bytes(long long pitch) {
+  return pitch * (C::B0 + 8 * C::BI);
+}
+template <class C>
+__host__ __device__ constexpr long long pop_plane_off(long long pitch, int i) {
+  return i == 0 ? 0 : pitch * (C::B0 + (i - 1) * C::BI);
+}
+
+__device__ __forceinline__ uint16_t enc16(__half, float v) { return __half_as_ushort(__float2half_rn(v)); }
+__device__ __forceinline__ uint16_t enc16(__nv_bfloat16, float v) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+__device__ __forceinline__ float dec16(__half, uint16_t q) { return __half2float(__ushort_as_half(q)); }
+__device__ __forceinline__ float dec16(__nv_bfloat16, uint16_t q) {
+  return __bfloat162float(__ushort_as_bfloat16(q));
+}
 
 template <typename T>
 struct Bufs {
-  const T* fin;   // 9 interleaved planes, post-collision f of t-1
-  const T* gin;
-  T* fout;        // STEP: post-collision f of t;  INIT: f^eq per node
-  T* gout;
+  const void* fin;  // population set (codec layout), post-collision f of t-1
+  const void* gin;
+  void* fout;       // STEP: post-collision f of t;  INIT: f^eq per node (plain)
+  void* gout;
   T* hist;        // 5 interleaved planes
   T* macro;       // NMACRO interleaved planes (MACRO)
   T* phi_prev;    // optional: phi(t) of the stepped time (STEP / HIST)
@@ -119,32 +171,119 @@ __device__ __forceinline__ long long ix(const Phys<T>& P, int NP, int k, int x, 
   return ((long long)y * NP + k) * P.pitch + XPAD + x;
 }
 
+// Decoded population i of node (x, r) of a set in codec C's layout.
+template <class C>
+__device__ __forceinline__ typename C::value_t pop_ld(const unsigned char* __restrict__ buf,
+                                                      const Phys<typename C::value_t>& P, int set, int i,
+                                                      int x, int r) {
+  using T = typename C::value_t;
+  const unsigned char* rb = buf + (long long)r * pop_row_bytes<C>(P.pitch);
+  if constexpr (!C::dev) {
+    return reinterpret_cast<const T*>(rb)[(long long)i * P.pitch + XPAD + x];
+  } else {
+    const float b = reinterpret_cast<const float*>(rb)[XPAD + x];
+    if (i == 0) return b;
+    const uint16_t q = reinterpret_cast<const uint16_t*>(rb + pop_plane_off<C>(P.pitch, i))[XPAD + x];
+    return fmaf(dec16(typename C::raw_t(), q), P.dv_is[set], P.dv_r[set][i >= 5] * b);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Pull the nine populations of node (x, r) from the post-collision planes,
 // with periodic wrap or half-way bounce-back at walls (Sec. 4).
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void pull9(const T* __restrict__ buf, const Phys<T>& P, int x, int r,
-                                      T out[9]) {
+template <class C>
+__device__ __forceinline__ void pull9(const void* buf_, const Phys<typename C::value_t>& P, int set, int x,
+                                      int r, typename C::value_t out[9]) {
+  using T = typename C::value_t;
   int xm = x - 1, xp = x + 1, ym = r - 1, yp = r + 1;
   bool bxm = false, bxp = false, bym = false, byp = false;
   if (xm < 0) { if (P.wall_x) bxm = true; else xm += P.nx; }
   if (xp >= P.nx) { if (P.wall_x) bxp = true; else xp -= P.nx; }
   if (ym < 0) { if (P.wall_y) bym = true; else ym += P.ny; }
   if (yp >= P.ny) { if (P.wall_y) byp = true; else yp -= P.ny; }
-  const long long pl = P.pitch;  // plane i of a row sits i * pitch after plane 0
-  const long long rc = (long long)r * 9 * pl + XPAD, rm = (long long)ym * 9 * pl + XPAD,
-                  rp = (long long)yp * 9 * pl + XPAD;
-  const long long c = rc + x;
-  out[0] = buf[c];
-  out[1] = buf[bxm ? 3 * pl + c : 1 * pl + rc + xm];
-  out[2] = buf[bym ? 4 * pl + c : 2 * pl + rm + x];
-  out[3] = buf[bxp ? 1 * pl + c : 3 * pl + rc + xp];
-  out[4] = buf[byp ? 2 * pl + c : 4 * pl + rp + x];
-  out[5] = buf[(bxm || bym) ? 7 * pl + c : 5 * pl + rm + xm];
-  out[6] = buf[(bxp || bym) ? 8 * pl + c : 6 * pl + rm + xp];
-  out[7] = buf[(bxp || byp) ? 5 * pl + c : 7 * pl + rp + xp];
-  out[8] = buf[(bxm || byp) ? 6 * pl + c : 8 * pl + rp + xm];
+  if constexpr (!C::dev) {
+    const T* buf = static_cast<const T*>(buf_);
+    const long long pl = P.pitch;  // plane i of a row sits i * pitch after plane 0
+    const long long rc = (long long)r * 9 * pl + XPAD, rm = (long long)ym * 9 * pl + XPAD,
+                    rp = (long long)yp * 9 * pl + XPAD;
+    const long long c = rc + x;
+    out[0] = buf[c];
+    out[1] = buf[bxm ? 3 * pl + c : 1 * pl + rc + xm];
+    out[2] = buf[bym ? 4 * pl + c : 2 * pl + rm + x];
+    out[3] = buf[bxp ? 1 * pl + c : 3 * pl + rc + xp];
+    out[4] = buf[byp ? 2 * pl + c : 4 * pl + rp + x];
+    out[5] = buf[(bxm || bym) ? 7 * pl + c : 5 * pl + rm + xm];
+    out[6] = buf[(bxp || bym) ? 8 * pl + c : 6 * pl + rm + xp];
+    out[7] = buf[(bxp || byp) ? 5 * pl + c : 7 * pl + rp + xp];
+    out[8] = buf[(bxm || byp) ? 6 * pl + c : 8 * pl + rp + xm];
+  } else {
+    const unsigned char* buf = static_cast<const unsigned char*>(buf_);
+    out[0] = pop_ld<C>(buf, P, set, 0, x, r);
+    out[1] = bxm ? pop_ld<C>(buf, P, set, 3, x, r) : pop_ld<C>(buf, P, set, 1, xm, r);
+    out[2] = bym ? pop_ld<C>(buf, P, set, 4, x, r) : pop_ld<C>(buf, P, set, 2, x, ym);
+    out[3] = bxp ? pop_ld<C>(buf, P, set, 1, x, r) : pop_ld<C>(buf, P, set, 3, xp, r);
+    out[4] = byp ? pop_ld<C>(buf, P, set, 2, x, r) : pop_ld<C>(buf, P, set, 4, x, yp);
+    out[5] = (bxm || bym) ? pop_ld<C>(buf, P, set, 7, x, r) : pop_ld<C>(buf, P, set, 5, xm, ym);
+    out[6] = (bxp || bym) ? pop_ld<C>(buf, P, set, 8, x, r) : pop_ld<C>(buf, P, set, 6, xp, ym);
+    out[7] = (bxp || byp) ? pop_ld<C>(buf, P, set, 5, x, r) : pop_ld<C>(buf, P, set, 7, xp, yp);
+    out[8] = (bxm || byp) ? pop_ld<C>(buf, P, set, 6, x, r) : pop_ld<C>(buf, P, set, 8, xm, yp);
+  }
+}
+
+// Encode and store the nine post-collision populations v of node (x, y)
+// into a set in codec C's layout, with the periodic copies in the row pads.
+// m0: the zeroth moment the stored populations must reproduce (phi for f;
+// used when conserve is set).
+template <class C>
+__device__ __forceinline__ void store_pops(const Phys<typename C::value_t>& P, void* buf_, int set, int x,
+                                           int y, const typename C::value_t v[9], typename C::value_t m0,
+                                           bool conserve) {
+  using T = typename C::value_t;
+  const long long pc = P.pitch;
+  const bool pads = !P.wall_x && (x < XPAD || x >= P.nx - XPAD);
+  const int off = x < XPAD ? P.nx : -P.nx;
+  const bool both = x < XPAD && x >= P.nx - XPAD;  // grids narrower than 2 XPAD: both pads
+  if constexpr (!C::dev) {
+    T* const o = static_cast<T*>(buf_) + ix(P, 9, 0, x, y);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) o[i * pc] = v[i];
+    if (pads) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) o[i * pc + off] = v[i];
+      if (both)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) o[i * pc - P.nx] = v[i];
+    }
+  } else {
+    using Q = typename C::raw_t;
+    const float s = P.dv_s[set], is = P.dv_is[set];
+    const float b = v[0];
+    uint16_t q[9];
+    float sq = 0.f;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+      q[i] = enc16(Q(), (v[i] - P.dv_r[set][i >= 5] * b) * s);
+      sq += dec16(Q(), q[i]) * is;
+    }
+    const float b0 = conserve ? P.dv_c0 * (m0 - sq) : b;
+    unsigned char* const rb = static_cast<unsigned char*>(buf_) + (long long)y * pop_row_bytes<C>(pc);
+    float* const o0 = reinterpret_cast<float*>(rb) + XPAD + x;
+    uint16_t* const oq = reinterpret_cast<uint16_t*>(rb + pop_plane_off<C>(pc, 1)) + XPAD + x;
+    *o0 = b0;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) oq[(i - 1) * pc] = q[i];
+    if (pads) {
+      o0[off] = b0;
+#pragma unroll
+      for (int i = 1; i < 9; ++i) oq[(i - 1) * pc + off] = q[i];
+      if (both) {
+        o0[-P.nx] = b0;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) oq[(i - 1) * pc - P.nx] = q[i];
+      }
+    }
+  }
 }
 
 template <typename T>
@@ -153,13 +292,13 @@ __device__ __forceinline__ T sum9(const T v[9]) {
 }
 
 // phi of the in-domain node (x, r) in a given mode.
-template <typename T, int MODE>
+template <class C, int MODE, typename T = typename C::value_t>
 __device__ __forceinline__ T phi_at(const Phys<T>& P, const Bufs<T>& B, int x, int r) {
   if (MODE == MODE_INIT) {
     return T(B.iphi[(long long)r * P.nx + x]);
   } else {
     T v[9];
-    pull9(B.fin, P, x, r, v);
+    pull9<C>(B.fin, P, 0, x, r, v);
     return sum9(v);
   }
 }
@@ -187,7 +326,8 @@ __device__ __forceinline__ T wall_ghost(const Phys<T>& P, int side, T phi1, T ph
 // 1 are 1 (s_f^k for k != 3, 5 and s_g^k for k = 0, 1, 2, 3, 5); those
 // moments then relax to m^eq + m_src / 2 without reading the populations'
 // own moments, which the general path (UR = false) computes and relaxes.
-template <typename T, int MODEL, int MODE, bool UR = false>
+// C: the storage codec of the STEP outputs (INIT writes plain values).
+template <class C, int MODEL, int MODE, bool UR = false, typename T = typename C::value_t>
 __device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, int x, int y,
                                             const T phi9[9], const T mu9[9], const T f[9],
                                             const T g[9], const T h[5], T u_in, T v_in, T p_in) {
@@ -451,36 +591,18 @@ __device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, 
     gs[7] = b - Xd - Yd + Qq; gs[8] = b + Xd - Yd - Qq;
   }
 
-  T* const fo = B.fout + ix(P, 9, 0, x, y);
-  T* const go = B.gout + ix(P, 9, 0, x, y);
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    fo[i * pc] = fs[i];
-    go[i * pc] = gs[i];
-  }
-  // periodic copies in the row pads (nodes within XPAD of an x edge)
-  if (!P.wall_x && (x < XPAD || x >= P.nx - XPAD)) {
-    const int off = x < XPAD ? P.nx : -P.nx;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      fo[i * pc + off] = fs[i];
-      go[i * pc + off] = gs[i];
-    }
-    if (x < XPAD && x >= P.nx - XPAD) {  // grids narrower than 2 XPAD: both pads
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        fo[i * pc - P.nx] = fs[i];
-        go[i * pc - P.nx] = gs[i];
-      }
-    }
-  }
+  using CS = typename std::conditional<MODE == MODE_INIT, PopPlain<T>, C>::type;
+  store_pops<CS>(P, B.fout, 0, x, y, fs, phi, true);
+  store_pops<CS>(P, B.gout, 1, x, y, gs, T(0), false);
 }
 
 // ---------------------------------------------------------------------------
 // The fused marching kernel.
 // ---------------------------------------------------------------------------
-template <typename T, int MODEL, int MODE>
-__global__ void __launch_bounds__(BX) k_march(const Phys<T> P, const Bufs<T> B) {
+template <class C, int MODEL, int MODE>
+__global__ void __launch_bounds__(BX) k_march(const Phys<typename C::value_t> P,
+                                              const Bufs<typename C::value_t> B) {
+  using T = typename C::value_t;
   constexpr int R = (MODEL == MODEL_CH) ? 2 : 1;  // phi halo radius
   constexpr int WS = BX + 2 * R;                  // phi ring row width
   __shared__ T sphi[RING][WS];
@@ -512,7 +634,7 @@ __global__ void __launch_bounds__(BX) k_march(const Phys<T> P, const Bufs<T> B) 
       if (MODE == MODE_INIT) {
         v = T(B.iphi[(long long)rr * nx + x]);
       } else {
-        pull9(B.fin, P, x, rr, fq[q]);
+        pull9<C>(B.fin, P, 0, x, rr, fq[q]);
         v = sum9(fq[q]);
       }
       sphi[s][tid + R] = v;
@@ -522,12 +644,12 @@ __global__ void __launch_bounds__(BX) k_march(const Phys<T> P, const Bufs<T> B) 
           int xh = x0 - k;
           T hv;
           if (xh >= 0) {
-            hv = phi_at<T, MODE>(P, B, xh, rr);
+            hv = phi_at<C, MODE>(P, B, xh, rr);
           } else if (!P.wall_x) {
-            hv = phi_at<T, MODE>(P, B, xh + nx, rr);
+            hv = phi_at<C, MODE>(P, B, xh + nx, rr);
           } else {  // ghost beyond the left wall, from columns 0 and 1
-            const T p1 = (x == 0) ? v : phi_at<T, MODE>(P, B, 0, rr);
-            hv = wall_ghost(P, SIDE_LEFT, p1, phi_at<T, MODE>(P, B, 1, rr));
+            const T p1 = (x == 0) ? v : phi_at<C, MODE>(P, B, 0, rr);
+            hv = wall_ghost(P, SIDE_LEFT, p1, phi_at<C, MODE>(P, B, 1, rr));
           }
           sphi[s][R - k] = hv;
         }
@@ -538,12 +660,12 @@ __global__ void __launch_bounds__(BX) k_march(const Phys<T> P, const Bufs<T> B) 
           int xh = x0 + w - 1 + k;
           T hv;
           if (xh < nx) {
-            hv = phi_at<T, MODE>(P, B, xh, rr);
+            hv = phi_at<C, MODE>(P, B, xh, rr);
           } else if (!P.wall_x) {
-            hv = phi_at<T, MODE>(P, B, xh - nx, rr);
+            hv = phi_at<C, MODE>(P, B, xh - nx, rr);
           } else {  // ghost beyond the right wall, from columns nx-1 and nx-2
-            const T p1 = (x == nx - 1) ? v : phi_at<T, MODE>(P, B, nx - 1, rr);
-            hv = wall_ghost(P, SIDE_RIGHT, p1, phi_at<T, MODE>(P, B, nx - 2, rr));
+            const T p1 = (x == nx - 1) ? v : phi_at<C, MODE>(P, B, nx - 1, rr);
+            hv = wall_ghost(P, SIDE_RIGHT, p1, phi_at<C, MODE>(P, B, nx - 2, rr));
           }
           sphi[s][w - 1 + R + k] = hv;
         }
@@ -641,7 +763,7 @@ __global__ void __launch_bounds__(BX) k_march(const Phys<T> P, const Bufs<T> B) 
         if (B.iuy) vin = T(B.iuy[di]);
         if (B.ip) pin = T(B.ip[di]);
       } else {
-        pull9(B.gin, P, x, y, g);
+        pull9<C>(B.gin, P, 1, x, y, g);
         if (MODE == MODE_STEP || MODE == MODE_MACRO) {
 #pragma unroll
           for (int k = 0; k < 5; ++k) h[k] = B.hist[ix(P, 5, k, x, y)];
@@ -697,7 +819,7 @@ __global__ void __launch_bounds__(BX) k_march(const Phys<T> P, const Bufs<T> B) 
         mu9[7] = smu[sm][cm - 1];
         mu9[8] = smu[sm][cm + 1];
       }
-      node_update<T, MODEL, MODE>(P, B, x, y, phi9, mu9, fq[0], g, h, uin, vin, pin);
+      node_update<C, MODEL, MODE>(P, B, x, y, phi9, mu9, fq[0], g, h, uin, vin, pin);
     }
     // advance the queue of pulled f
 #pragma unroll
@@ -736,17 +858,23 @@ struct Seg {
 constexpr int TRING = 4;
 __host__ __device__ constexpr int tslot(int r) { return (r + 2 * TRING) & (TRING - 1); }
 
-template <typename T, int TBX, int DF, int DG>
+// A staged row slot holds the segment of each of the nine planes: plane 0
+// (SEG elements of B0 bytes) then planes 1..8 (SEG elements of BI bytes).
+template <class C, int TBX, int DF, int DG>
 struct TmaLayout {
+  using T = typename C::value_t;
   static constexpr int SEG = Seg<TBX>::value;
   static constexpr int RF = 4 + DF, RG = 3 + DG;
+  static constexpr size_t P0 = (size_t)SEG * C::B0;   // bytes of plane 0's segment
+  static constexpr size_t PI = (size_t)SEG * C::BI;   // bytes of each other plane's segment
+  static constexpr size_t SLOT = P0 + 8 * PI;
   static constexpr size_t f_off = 0;
-  static constexpr size_t g_off = f_off + sizeof(T) * RF * 9 * SEG;
-  static constexpr size_t phi_off = g_off + sizeof(T) * RG * 9 * SEG;
+  static constexpr size_t g_off = f_off + RF * SLOT;
+  static constexpr size_t phi_off = g_off + RG * SLOT;
   static constexpr size_t bar_off = phi_off + sizeof(T) * TRING * (TBX + 2);
   static constexpr size_t bytes = bar_off + 8 * (RF + RG);
   static_assert(g_off % 16 == 0 && phi_off % 16 == 0 && bar_off % 8 == 0, "smem layout alignment");
-  static_assert((SEG * sizeof(T)) % 16 == 0, "bulk-copy rows must be 16-byte multiples");
+  static_assert(P0 % 16 == 0 && PI % 16 == 0, "bulk-copy segments must be 16-byte multiples");
 };
 // Each try_wait suspends for at most ~1 us (the hint), so a wait gives up
 // after about a second; a normal row arrives within microseconds.
@@ -801,31 +929,75 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
-// Pull of the node in staged column c (row rr) from the source-row slots
-// rm, r0, rp (rows rr-1, rr, rr+1); bounce-back where the source lies beyond
-// a wall.  xg is the node's global column (for the x-wall test).
-template <int SEG, typename T>
-__device__ __forceinline__ void pull_staged(const T* rm, const T* r0, const T* rp, int c, bool bxm, bool bxp,
-                                            bool bym, bool byp, T out[9]) {
-  out[0] = r0[0 * SEG + c];
-  out[1] = bxm ? r0[3 * SEG + c] : r0[1 * SEG + c - 1];
-  out[2] = bym ? r0[4 * SEG + c] : rm[2 * SEG + c];
-  out[3] = bxp ? r0[1 * SEG + c] : r0[3 * SEG + c + 1];
-  out[4] = byp ? r0[2 * SEG + c] : rp[4 * SEG + c];
-  out[5] = (bxm || bym) ? r0[7 * SEG + c] : rm[5 * SEG + c - 1];
-  out[6] = (bxp || bym) ? r0[8 * SEG + c] : rm[6 * SEG + c + 1];
-  out[7] = (bxp || byp) ? r0[5 * SEG + c] : rp[7 * SEG + c + 1];
-  out[8] = (bxm || byp) ? r0[6 * SEG + c] : rp[8 * SEG + c - 1];
+// Decoded population i in staged column c of a slot.
+template <class C, int SEG>
+__device__ __forceinline__ typename C::value_t stg_ld(const unsigned char* slot, int i, int c,
+                                                      const typename C::value_t* r2,
+                                                      typename C::value_t is) {
+  using T = typename C::value_t;
+  if constexpr (!C::dev) {
+    return reinterpret_cast<const T*>(slot)[i * SEG + c];
+  } else {
+    const float b = reinterpret_cast<const float*>(slot)[c];
+    if (i == 0) return b;
+    const uint16_t q = reinterpret_cast<const uint16_t*>(slot + SEG * C::B0)[(i - 1) * SEG + c];
+    return fmaf(dec16(typename C::raw_t(), q), is, r2[i >= 5] * b);
+  }
 }
 
-template <typename T, bool UR, int TBX, int DF, int DG>
-__global__ void __launch_bounds__(TBX, (sizeof(T) == 4 ? 640 : 256) / TBX)
-    k_step_tma(const Phys<T> P, const Bufs<T> B, int* __restrict__ err) {
-  using L = TmaLayout<T, TBX, DF, DG>;
+// Pull of the node in staged column c from the source-row slots rm, r0, rp
+// (rows rr-1, rr, rr+1); bounce-back where the source lies beyond a wall.
+// r2, is: the set's deviation ratios and inverse scale (PopDev only).
+template <class C, int SEG, typename T = typename C::value_t>
+__device__ __forceinline__ void pull_staged(const unsigned char* rm, const unsigned char* r0,
+                                            const unsigned char* rp, int c, bool bxm, bool bxp, bool bym,
+                                            bool byp, const T* r2, T is, T out[9]) {
+  out[0] = stg_ld<C, SEG>(r0, 0, c, r2, is);
+  out[1] = bxm ? stg_ld<C, SEG>(r0, 3, c, r2, is) : stg_ld<C, SEG>(r0, 1, c - 1, r2, is);
+  out[2] = bym ? stg_ld<C, SEG>(r0, 4, c, r2, is) : stg_ld<C, SEG>(rm, 2, c, r2, is);
+  out[3] = bxp ? stg_ld<C, SEG>(r0, 1, c, r2, is) : stg_ld<C, SEG>(r0, 3, c + 1, r2, is);
+  out[4] = byp ? stg_ld<C, SEG>(r0, 2, c, r2, is) : stg_ld<C, SEG>(rp, 4, c, r2, is);
+  out[5] = (bxm || bym) ? stg_ld<C, SEG>(r0, 7, c, r2, is) : stg_ld<C, SEG>(rm, 5, c - 1, r2, is);
+  out[6] = (bxp || bym) ? stg_ld<C, SEG>(r0, 8, c, r2, is) : stg_ld<C, SEG>(rm, 6, c + 1, r2, is);
+  out[7] = (bxp || byp) ? stg_ld<C, SEG>(r0, 5, c, r2, is) : stg_ld<C, SEG>(rp, 7, c + 1, r2, is);
+  out[8] = (bxm || byp) ? stg_ld<C, SEG>(r0, 6, c, r2, is) : stg_ld<C, SEG>(rp, 8, c - 1, r2, is);
+}
+
+// Launch shape of the TMA step per storage codec: strip width, rows staged
+// ahead of need (f, g), resident threads per SM it is compiled for
+// (registers), and whether the f pulled for phi of row y+1 is kept in
+// registers for that row's collision instead of being pulled again.
+//   FP32: 160 columns, one row ahead, 4 blocks (20 warps) per SM: shared
+//         memory (56 KB a block) is the occupancy limit.
+//   FP64: 160 columns, one row ahead, one block per SM (registers).
+//   16-bit deviations: 128 columns, two rows ahead, 6 blocks (24 warps) per
+//         SM; the rows are 44 % smaller, so more blocks fit, and keeping f
+//         saves the second decode.
+// Measured on the 16384^2 step (GLUPS): FP32 160/1/1 29.5-30.6 against 128
+// to 256 columns, deeper staging or more blocks 24.9-28.2.  FP16 deviations
+// 128/2/2 x6 with kept f 34.4; 160/1/1 x4 30.3; 160/2/2 x5 32.3, with kept
+// f 33.4; 96/2/2 x8 33.1; 256/2/2 x3 32.5; history staged by TMA or copies
+// issued from every warp 27-29.
+template <class C>
+struct TmaCfg {
+  static constexpr int TBX = C::dev ? 128 : 160;
+  static constexpr int DF = C::dev ? 2 : 1, DG = C::dev ? 2 : 1;
+  static constexpr int threads = C::dev ? 768 : (sizeof(typename C::value_t) == 4 ? 640 : 256);
+  static constexpr bool keep_f = C::dev;
+};
+
+template <class C, bool UR>
+__global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>::TBX)
+    k_step_tma(const Phys<typename C::value_t> P, const Bufs<typename C::value_t> B, int* __restrict__ err) {
+  using T = typename C::value_t;
+  constexpr int TBX = TmaCfg<C>::TBX, DF = TmaCfg<C>::DF, DG = TmaCfg<C>::DG;
+  constexpr bool FK = TmaCfg<C>::keep_f;
+  using L = TmaLayout<C, TBX, DF, DG>;
   constexpr int SEG = L::SEG, RF = L::RF, RG = L::RG;
+  constexpr int FS = (int)L::SLOT;  // bytes per row slot
   extern __shared__ __align__(128) unsigned char smem[];
-  T* const sf = reinterpret_cast<T*>(smem + L::f_off);    // [RF][9][SEG]
-  T* const sg = reinterpret_cast<T*>(smem + L::g_off);    // [RG][9][SEG]
+  unsigned char* const sf = smem + L::f_off;              // [RF] row slots
+  unsigned char* const sg = smem + L::g_off;              // [RG] row slots
   T* const sp = reinterpret_cast<T*>(smem + L::phi_off);  // [TRING][TBX + 2]
   uint64_t* const barF = reinterpret_cast<uint64_t*>(smem + L::bar_off);
   uint64_t* const barG = barF + RF;
@@ -839,8 +1011,13 @@ __global__ void __launch_bounds__(TBX, (sizeof(T) == 4 ? 640 : 256) / TBX)
   const int x = x0 + tid;
   const bool wx = P.wall_x != 0, wy = P.wall_y != 0;
   const int fbase = y0 - 2, gbase = y0 - 1;  // first staged f / g row
-  constexpr int VE = 16 / (int)sizeof(T);
-  const uint32_t seg_bytes = (uint32_t)(((w + 2 * XPAD + VE - 1) / VE) * VE * (int)sizeof(T));
+  // bytes copied per plane segment: [x0 - XPAD, x0 + w + XPAD) rounded up to 16
+  const uint32_t seg0 = (uint32_t)((((w + 2 * XPAD) * C::B0 + 15) / 16) * 16);
+  const uint32_t segI = (uint32_t)((((w + 2 * XPAD) * C::BI + 15) / 16) * 16);
+  const long long RB = pop_row_bytes<C>(P.pitch);
+  // deviation constants of the two sets (unused by PopPlain)
+  const T rf2[2] = {P.dv_r[0][0], P.dv_r[0][1]}, rg2[2] = {P.dv_r[1][0], P.dv_r[1][1]};
+  const T isf = P.dv_is[0], isg = P.dv_is[1];
   const int f_last = y1 + 1, g_last = y1;  // last f / g row any output row needs
   const bool edge_x = wx && (x0 == 0 || x0 + w == nx);  // strip touches an x wall
 
@@ -852,18 +1029,22 @@ __global__ void __launch_bounds__(TBX, (sizeof(T) == 4 ? 640 : 256) / TBX)
 
   auto wrap_row = [&](int r) { return r < 0 ? r + ny : (r >= ny ? r - ny : r); };
   // producer side (thread 0 only)
-  auto stage = [&](const T* src, T* slot, uint64_t* bar, int r) {
+  auto stage = [&](const void* src, unsigned char* slot, uint64_t* bar, int r) {
     if ((r < 0 || r >= ny) && wy) {  // beyond a wall: nothing to load, complete the phase
       mbar_arrive(bar);
       return;
     }
-    const T* row = src + (long long)wrap_row(r) * 9 * P.pitch + x0;  // element x0 - XPAD, plane 0
-    mbar_arrive_expect_tx(bar, 9u * seg_bytes);
+    // element x0 - XPAD of the row's planes
+    const unsigned char* row = static_cast<const unsigned char*>(src) + (long long)wrap_row(r) * RB;
+    mbar_arrive_expect_tx(bar, seg0 + 8u * segI);
+    bulk_g2s(slot, row + (long long)x0 * C::B0, seg0, bar);
 #pragma unroll 1
-    for (int i = 0; i < 9; ++i) bulk_g2s(slot + i * SEG, row + i * P.pitch, seg_bytes, bar);
+    for (int i = 1; i < 9; ++i)
+      bulk_g2s(slot + L::P0 + (i - 1) * L::PI, row + pop_plane_off<C>(P.pitch, i) + (long long)x0 * C::BI,
+               segI, bar);
   };
-  auto fslot = [&](int r) { return sf + ((r - fbase) % RF) * (9 * SEG); };
-  auto gslot = [&](int r) { return sg + ((r - gbase) % RG) * (9 * SEG); };
+  auto fslot = [&](int r) { return sf + ((r - fbase) % RF) * FS; };
+  auto gslot = [&](int r) { return sg + ((r - gbase) % RG) * FS; };
   auto stage_f = [&](int r) { stage(B.fin, fslot(r), &barF[(r - fbase) % RF], r); };
   auto stage_g = [&](int r) { stage(B.gin, gslot(r), &barG[(r - gbase) % RG], r); };
   auto wait_f = [&](int r) {
@@ -878,25 +1059,31 @@ __global__ void __launch_bounds__(TBX, (sizeof(T) == 4 ? 640 : 256) / TBX)
   // phi of row r (in the domain, or wrapped) into the phi ring: own column,
   // left halo (thread 0), right halo (thread w - 1); x-wall ghosts from the
   // thread's own phi and a second pull of the neighbouring column.
-  auto phi_row_at = [&](int r, const T* rm, const T* r0, const T* rp) {
+  T fnext[9];  // FK: the pulled f of the last phi row made with keep set
+  auto phi_row_at = [&](int r, const unsigned char* rm, const unsigned char* r0, const unsigned char* rp,
+                        bool keep) {
     const int rr = wrap_row(r);
     const bool bym = wy && rr == 0, byp = wy && rr == ny - 1;
     T* dst = sp + tslot(r) * (TBX + 2);
     if (!active) return;
     T v[9];
     if (edge_x || bym || byp)
-      pull_staged<SEG>(rm, r0, rp, tid + XPAD, wx && x == 0, wx && x == nx - 1, bym, byp, v);
+      pull_staged<C, SEG>(rm, r0, rp, tid + XPAD, wx && x == 0, wx && x == nx - 1, bym, byp, rf2, isf, v);
     else
-      pull_staged<SEG>(rm, r0, rp, tid + XPAD, false, false, false, false, v);
+      pull_staged<C, SEG>(rm, r0, rp, tid + XPAD, false, false, false, false, rf2, isf, v);
     const T ph = sum9(v);
     dst[tid + 1] = ph;
+    if (FK && keep) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) fnext[i] = v[i];
+    }
     if (tid == 0) {
       T hv;
       if (x0 > 0 || !wx) {
-        pull_staged<SEG>(rm, r0, rp, XPAD - 1, false, wx && x0 - 1 == nx - 1, bym, byp, v);
+        pull_staged<C, SEG>(rm, r0, rp, XPAD - 1, false, wx && x0 - 1 == nx - 1, bym, byp, rf2, isf, v);
         hv = sum9(v);
       } else {
-        pull_staged<SEG>(rm, r0, rp, XPAD + 1, false, wx && 1 == nx - 1, bym, byp, v);
+        pull_staged<C, SEG>(rm, r0, rp, XPAD + 1, false, wx && 1 == nx - 1, bym, byp, rf2, isf, v);
         hv = wall_ghost(P, SIDE_LEFT, ph, sum9(v));
       }
       dst[0] = hv;
@@ -904,16 +1091,16 @@ __global__ void __launch_bounds__(TBX, (sizeof(T) == 4 ? 640 : 256) / TBX)
     if (tid == w - 1) {
       T hv;
       if (x0 + w < nx || !wx) {
-        pull_staged<SEG>(rm, r0, rp, XPAD + w, wx && x0 + w == 0, wx && x0 + w == nx - 1, bym, byp, v);
+        pull_staged<C, SEG>(rm, r0, rp, XPAD + w, wx && x0 + w == 0, wx && x0 + w == nx - 1, bym, byp, rf2, isf, v);
         hv = sum9(v);
       } else {
-        pull_staged<SEG>(rm, r0, rp, XPAD + w - 2, wx && nx - 2 == 0, false, bym, byp, v);
+        pull_staged<C, SEG>(rm, r0, rp, XPAD + w - 2, wx && nx - 2 == 0, false, bym, byp, rf2, isf, v);
         hv = wall_ghost(P, SIDE_RIGHT, ph, sum9(v));
       }
       dst[w + 1] = hv;
     }
   };
-  auto phi_row = [&](int r) { phi_row_at(r, fslot(r - 1), fslot(r), fslot(r + 1)); };
+  auto phi_row = [&](int r) { phi_row_at(r, fslot(r - 1), fslot(r), fslot(r + 1), r == y0); };
   auto ghost_row = [&](int rg, int r1, int r2, int side) {
     T* d = sp + tslot(rg) * (TBX + 2);
     const T* a = sp + tslot(r1) * (TBX + 2);
@@ -956,17 +1143,21 @@ __global__ void __launch_bounds__(TBX, (sizeof(T) == 4 ? 640 : 256) / TBX)
   int fA = 1 % RF, gA = 0;                   // rows y0-1 (f: local 1, g: local 0)
   int fW = 4 % RF, fWp = (4 / RF) & 1;       // f row y0+2 (local 4)
   int gW = 2 % RG, gWp = (2 / RG) & 1;       // g row y0+1 (local 2)
-  constexpr int FS = 9 * SEG;
   for (int y = y0; y < y1 && !failed; ++y) {
     ok = true;
     if (y + 2 <= f_last) ok = mbar_wait_bounded(&barF[fW], fWp) && ok;
     if (y + 1 <= g_last) ok = mbar_wait_bounded(&barG[gW], gWp) && ok;
-    const T* f_m = sf + fA * FS;                 // f row y-1
-    const T* f_0 = sf + add(fA, 1, RF) * FS;     // f row y
-    const T* f_p = sf + add(fA, 2, RF) * FS;     // f row y+1
+    T f[9];  // pulled f of row y (FK: made with phi of row y)
+    if (FK) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) f[i] = fnext[i];
+    }
+    const unsigned char* f_m = sf + fA * FS;                 // f row y-1
+    const unsigned char* f_0 = sf + add(fA, 1, RF) * FS;     // f row y
+    const unsigned char* f_p = sf + add(fA, 2, RF) * FS;     // f row y+1
     // phi of row y+1 (a ghost row above a top wall)
     const int r1 = y + 1;
-    if (r1 < ny || !wy) phi_row_at(r1, f_0, f_p, sf + add(fA, 3, RF) * FS);
+    if (r1 < ny || !wy) phi_row_at(r1, f_0, f_p, sf + add(fA, 3, RF) * FS, true);
     else if (r1 == ny) ghost_row(ny, ny - 1, ny - 2, SIDE_TOP);  // rows ny-1, ny-2 ready since the last barrier
     failed = __syncthreads_or(!ok);
     if (failed) break;
@@ -1002,20 +1193,20 @@ __global__ void __launch_bounds__(TBX, (sizeof(T) == 4 ? 640 : 256) / TBX)
       phi9[6] = pp[c - 1];
       phi9[7] = pm[c - 1];
       phi9[8] = pm[c + 1];
-      const T* g_m = sg + gA * FS;
-      const T* g_0 = sg + add(gA, 1, RG) * FS;
-      const T* g_p = sg + add(gA, 2, RG) * FS;
+      const unsigned char* g_m = sg + gA * FS;
+      const unsigned char* g_0 = sg + add(gA, 1, RG) * FS;
+      const unsigned char* g_p = sg + add(gA, 2, RG) * FS;
       const bool bym = wy && y == 0, byp = wy && y == ny - 1;
-      T f[9], g[9];
+      T g[9];
       if (edge_x || bym || byp) {  // bounce-back links possible (block-uniform test)
         const bool bxm = wx && x == 0, bxp = wx && x == nx - 1;
-        pull_staged<SEG>(f_m, f_0, f_p, tid + XPAD, bxm, bxp, bym, byp, f);
-        pull_staged<SEG>(g_m, g_0, g_p, tid + XPAD, bxm, bxp, bym, byp, g);
+        if (!FK) pull_staged<C, SEG>(f_m, f_0, f_p, tid + XPAD, bxm, bxp, bym, byp, rf2, isf, f);
+        pull_staged<C, SEG>(g_m, g_0, g_p, tid + XPAD, bxm, bxp, bym, byp, rg2, isg, g);
       } else {
-        pull_staged<SEG>(f_m, f_0, f_p, tid + XPAD, false, false, false, false, f);
-        pull_staged<SEG>(g_m, g_0, g_p, tid + XPAD, false, false, false, false, g);
+        if (!FK) pull_staged<C, SEG>(f_m, f_0, f_p, tid + XPAD, false, false, false, false, rf2, isf, f);
+        pull_staged<C, SEG>(g_m, g_0, g_p, tid + XPAD, false, false, false, false, rg2, isg, g);
       }
-      node_update<T, MODEL_AC, MODE_STEP, UR>(P, B, x, y, phi9, phi9, f, g, h, T(0), T(0), T(0));
+      node_update<C, MODEL_AC, MODE_STEP, UR>(P, B, x, y, phi9, phi9, f, g, h, T(0), T(0), T(0));
     }
 #pragma unroll
     for (int k = 0; k < 5; ++k) h[k] = hn[k];
@@ -1049,7 +1240,7 @@ __global__ void k_pull(const Phys<T> P, const T* __restrict__ in, T* __restrict_
   const int y = blockIdx.y;
   if (x >= P.nx) return;
   T v[9];
-  pull9(in, P, x, y, v);
+  pull9<PopPlain<T>>(in, P, 0, x, y, v);
   T* o = out + ix(P, 9, 0, x, y);
 #pragma unroll
   for (int i = 0; i < 9; ++i) o[i * P.pitch] = v[i];
@@ -1081,6 +1272,47 @@ __global__ void k_unstream(const Phys<T> P, const T* __restrict__ in, T* __restr
       if (dx >= P.nx - XPAD) out[d - P.nx] = val;
     }
   }
+}
+
+// Deviation storage: the pulled population k of the nodes of the region
+// [x0, x0+w) x [y0, y0+hgt), decoded, as dense doubles plus add.
+template <class C>
+__global__ void k_pull_export(const Phys<typename C::value_t> P, const void* __restrict__ in, int set, int k,
+                              double* __restrict__ out, double add, int x0, int y0, int w, int hgt) {
+  using T = typename C::value_t;
+  const int xx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int yy = blockIdx.y;
+  if (xx >= w) return;
+  T v[9];
+  pull9<C>(in, P, set, x0 + xx, y0 + yy, v);
+  out[(long long)yy * w + xx] = double(v[k]) + add;
+}
+
+// Deviation storage: the inverse of the pull, node by node.  Slot j of
+// node s receives the value node s + c_j pulls in direction j, or, where
+// s + c_j lies beyond a wall, the value s itself pulls in direction opp(j);
+// the node's nine slots are then encoded together (for f with the node's
+// zeroth moment kept exact).
+template <class C>
+__global__ void k_restream(const Phys<typename C::value_t> P, const typename C::value_t* __restrict__ in,
+                           void* __restrict__ out, int set) {
+  using T = typename C::value_t;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= P.nx) return;
+  const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  const int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  const int op[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+  T v[9];
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    int tx = x + cx[j], ty = y + cy[j];
+    bool wall = false;
+    if (tx < 0 || tx >= P.nx) { if (P.wall_x) wall = true; else tx = (tx + P.nx) % P.nx; }
+    if (ty < 0 || ty >= P.ny) { if (P.wall_y) wall = true; else ty = (ty + P.ny) % P.ny; }
+    v[j] = wall ? in[ix(P, 9, op[j], x, y)] : in[ix(P, 9, j, tx, ty)];
+  }
+  store_pops<C>(P, out, set, x, y, v, sum9(v), set == 0);
 }
 
 // plane k of a set of NP interleaved planes -> dense doubles of the region

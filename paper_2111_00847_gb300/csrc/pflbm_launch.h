@@ -1,6 +1,9 @@
 // Host-side launch wrappers of the device kernels (defined in
-// pflbm_launch.cuh, instantiated for float and double in pflbm_f32.cu and
-// pflbm_f64.cu).
+// pflbm_launch.cuh).  C is a population storage codec (PopPlain<float>,
+// PopPlain<double>, PopDev<__half>, PopDev<__nv_bfloat16>); each is
+// instantiated in a translation unit of its own (pflbm_f32.cu, pflbm_f64.cu,
+// pflbm_f16.cu, pflbm_bf16.cu).  T-typed wrappers handle the planes kept in
+// the arithmetic type (history, macroscopic fields, diagnostics).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -9,12 +12,22 @@
 
 namespace pflbm {
 
-template <typename T>
-cudaError_t launch_march(int model, int mode, const Phys<T>& P, const Bufs<T>& B, cudaStream_t s);
+template <class C>
+cudaError_t launch_march(int model, int mode, const Phys<typename C::value_t>& P,
+                         const Bufs<typename C::value_t>& B, cudaStream_t s);
 // TMA-staged Allen-Cahn step (returns cudaErrorNotSupported when the grid is
 // too narrow for it; the caller then uses launch_march)
-template <typename T>
-cudaError_t launch_step_tma(const Phys<T>& P, const Bufs<T>& B, int* err, bool unit_rates, cudaStream_t s);
+template <class C>
+cudaError_t launch_step_tma(const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B, int* err,
+                            bool unit_rates, cudaStream_t s);
+// deviation storage: pulled plane k of a set -> dense doubles of a region
+template <class C>
+cudaError_t launch_pull_export(const Phys<typename C::value_t>& P, const void* in, int set, int k, double* out,
+                               double add, int x0, int y0, int w, int hgt, cudaStream_t s);
+// deviation storage: pulled values (9 plain planes) -> encoded post-collision set
+template <class C>
+cudaError_t launch_restream(const Phys<typename C::value_t>& P, const typename C::value_t* in, void* out,
+                            int set, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pull(const Phys<T>& P, const T* in, T* out, cudaStream_t s);
 template <typename T>

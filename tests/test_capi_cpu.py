@@ -64,7 +64,7 @@ def _bad(prm_kw):
     (dict(nx=2), -1), (dict(ny=0), -1), (dict(phiA=0.0), -1), (dict(rhoA=-1.0), -1),
     (dict(bc=(1, 0, 0, 0)), -1), (dict(theta_deg=(90, 90, 200, 90)), -1),
     (dict(s_f=(1.0, 1.0, 1.0, 2.5, 1, 1, 1, 1, 1)), -1), (dict(width=0.5), -1),
-    (dict(precision=W.PREC_FP16_DEV), -5), (dict(flux_model=W.FLUX_CORRECTED), -5),
+    (dict(precision=7), -1), (dict(flux_model=W.FLUX_CORRECTED), -5),
     (dict(phase_model=7), -1), (dict(nx=70000, ny=70000), -1), (dict(flags=8), -1),
 ])
 def test_create_rejects_bad_parameters(pk, kw, code):
