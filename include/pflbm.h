@@ -233,6 +233,41 @@ void lbm_destroy(lbm_handle *h);
  * h is NULL).  Valid until the next call on the handle. */
 const char *lbm_last_error(const lbm_handle *h);
 
+/* ---- Snapshots and the discrete adjoint (an extension beyond the paper) ----
+ *
+ * The state after t steps is (f*, g*, chi): the post-collision populations
+ * and the history of the explicit-Euler time derivatives (App. C).  A
+ * snapshot holds it byte for byte: lbm_state_bytes(h) bytes of DEVICE
+ * memory on the handle's device, written and read in order on the handle's
+ * stream (the caller owns the memory; no synchronisation is implied).
+ * lbm_restore also sets the step counter to t.  The diagnostics' phi(t-1)
+ * is not part of the state. */
+int64_t lbm_state_bytes(const lbm_handle *h);
+int lbm_snapshot(lbm_handle *h, void *dst);
+int lbm_restore(lbm_handle *h, const void *src, int64_t t);
+
+/* Reverse mode of lbm_step for an objective J(phi_N) of the phase field
+ * after N steps (Allen-Cahn model, FP64 or FP32 storage; otherwise
+ * LBM_EUNSUPPORTED).  The handle keeps the adjoint lambda of the state.
+ *   lbm_adjoint_seed(h, dJ_dphi)  host [ny][nx] doubles dJ/dphi_N:
+ *       lambda := dJ/ds_N through phi_N = sum of the pulled f (Eq. (22a));
+ *       zeroes the accumulated dJ/dG.
+ *   lbm_adjoint_step(h, state)  state = device snapshot of s_t, the input of
+ *       the step t -> t+1: lambda_{t+1} -> lambda_t, and adds the step's
+ *       dJ/dG (G the body force of F = mu_phi grad phi + G, i.e. (gx, gy)
+ *       scaled by the gravity mode).  Call for t = N-1 down to 0.
+ *   lbm_adjoint_init(h, state0, dJ_dphi0)  state0 = device snapshot taken
+ *       right after lbm_init_fields(phi0, NULL, NULL, p): writes dJ/dphi0 to
+ *       host [ny][nx] doubles (LBM_EUNSUPPORTED if that init had a velocity)
+ *       and adds the set-up's dJ/dG.
+ *   lbm_adjoint_gravity(h, dJ_dG)  host double[2]: dJ/dgx, dJ/dgy so far.
+ * The step is smooth except where the wetting root's discriminant is
+ * clamped; there the clamp's derivative is taken as zero. */
+int lbm_adjoint_seed(lbm_handle *h, const double *dJ_dphi);
+int lbm_adjoint_step(lbm_handle *h, const void *state);
+int lbm_adjoint_init(lbm_handle *h, const void *state0, double *dJ_dphi0);
+int lbm_adjoint_gravity(lbm_handle *h, double *dJ_dG);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,7 +12,7 @@ derivatives:
   phi = sum f (Eq. (22a)); ghost ring of phi (x sides first, then y sides
   over the extended x range; wetting ghosts from Eqs. (49)-(50)); isotropic
   grad and Laplacian (Eqs. (C.9)-(C.10)); mu_phi (Eq. (5)); Allen-Cahn
-  lambda, n, D (Eqs. (7)-(8), n = grad phi / max(|grad phi|, delta_n));
+  lambda, n, D (Eqs. (7)-(8), n = grad phi / (|grad phi|^4 + delta_n^4)^(1/4));
   rho, nu (Eqs. (10)-(12)); m^{phi C} (Eq. (15)); F = mu grad phi + G;
   u (Eq. (22b)); p (Eq. (39), second way of Remark 1); MRT collisions
   (Eqs. (17), (40) with the moment vectors of Eqs. (C.2)-(C.4)); pull
@@ -68,7 +68,7 @@ class TorchScheme:
         self.lam_coef = (math.sqrt(2.0 * self.beta / self.kappa) if prm.sigma > 0
                          else 4.0 / (prm.width * dphi))                   # Eq. (8)
         self.drho = (prm.rhoA - prm.rhoB) / dphi                          # Eq. (10)
-        self.delta_n = 1e-3 * dphi / prm.width
+        self.delta_n = 5e-3 * dphi / prm.width
         sfm = 1.0 / (prm.mobility / (prm.eta * CS2) + 0.5)
         self.Sf = [(sfm if k in (3, 5) else 1.0) if math.isnan(prm.s_f[k]) else prm.s_f[k] for k in range(9)]
         self.Sg = [1.0 if math.isnan(prm.s_g[k]) else prm.s_g[k] for k in range(9)]
@@ -129,7 +129,8 @@ class TorchScheme:
         gx, gy, lap = self.stencils(phi)
         mu = 4.0 * self.beta * (phi - p.phiA) * (phi - p.phiB) * (phi - 0.5 * (p.phiA + p.phiB)) - self.kappa * lap
         lam = self.lam_coef * (p.phiA - phi) * (phi - p.phiB)
-        gm = torch.sqrt(torch.clamp(gx * gx + gy * gy, min=self.delta_n ** 2))
+        g2 = gx * gx + gy * gy
+        gm = torch.sqrt(torch.sqrt(g2 * g2 + self.delta_n ** 4))
         nxv, nyv = gx / gm, gy / gm
         Dx, Dy = gx - lam * nxv, gy - lam * nyv
         rho = self.drho * (phi - p.phiB) + p.rhoB

@@ -33,7 +33,9 @@ DIAG_KEYS = ("t", "sum_phi", "Du_rms", "Sm_rms", "umax", "nonfinite", "n_avg", "
 
 EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_fields", "lbm_fields_region",
             "lbm_fields_noalloc", "lbm_set_fields",
-            "lbm_time", "lbm_device_bytes", "lbm_destroy", "lbm_last_error")
+            "lbm_time", "lbm_device_bytes", "lbm_destroy", "lbm_last_error",
+            "lbm_state_bytes", "lbm_snapshot", "lbm_restore", "lbm_adjoint_seed", "lbm_adjoint_step",
+            "lbm_adjoint_init", "lbm_adjoint_gravity")
 
 
 class LbmParams(C.Structure):
@@ -92,6 +94,14 @@ def load(path: str | None = None):
     L.lbm_destroy.restype = None
     L.lbm_last_error.argtypes = [C.c_void_p]
     L.lbm_last_error.restype = C.c_char_p
+    L.lbm_state_bytes.argtypes = [C.c_void_p]
+    L.lbm_state_bytes.restype = C.c_int64
+    L.lbm_snapshot.argtypes = [C.c_void_p, C.c_void_p]
+    L.lbm_restore.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+    L.lbm_adjoint_seed.argtypes = [C.c_void_p, dp]
+    L.lbm_adjoint_step.argtypes = [C.c_void_p, C.c_void_p]
+    L.lbm_adjoint_init.argtypes = [C.c_void_p, C.c_void_p, dp]
+    L.lbm_adjoint_gravity.argtypes = [C.c_void_p, dp]
     _lib = L
     return L
 
@@ -182,6 +192,35 @@ def lbm_device_bytes(h) -> int:
 
 def lbm_destroy(h):
     load().lbm_destroy(h)
+
+
+def lbm_state_bytes(h) -> int:
+    return int(load().lbm_state_bytes(h))
+
+
+def lbm_snapshot(h, dst_ptr: int):
+    """Copy the state into device memory at dst_ptr (lbm_state_bytes bytes)."""
+    _check(load().lbm_snapshot(h, C.c_void_p(int(dst_ptr))), h)
+
+
+def lbm_restore(h, src_ptr: int, t: int):
+    _check(load().lbm_restore(h, C.c_void_p(int(src_ptr)), int(t)), h)
+
+
+def lbm_adjoint_seed(h, dj_dphi: np.ndarray):
+    _check(load().lbm_adjoint_seed(h, _dptr(dj_dphi)), h)
+
+
+def lbm_adjoint_step(h, state_ptr: int):
+    _check(load().lbm_adjoint_step(h, C.c_void_p(int(state_ptr))), h)
+
+
+def lbm_adjoint_init(h, state0_ptr: int, out: np.ndarray):
+    _check(load().lbm_adjoint_init(h, C.c_void_p(int(state0_ptr)), _dptr(out)), h)
+
+
+def lbm_adjoint_gravity(h, out: np.ndarray):
+    _check(load().lbm_adjoint_gravity(h, _dptr(out)), h)
 
 
 # ---- PyTorch plumbing --------------------------------------------------------
@@ -303,6 +342,39 @@ class Simulation:
 
     def diag(self) -> dict:
         return dict(zip(DIAG_KEYS, self.fields(LBM_DIAG).tolist()))
+
+    # -- snapshots and the adjoint (device buffers are torch uint8 tensors)
+    @property
+    def state_bytes(self) -> int:
+        return lbm_state_bytes(self._h)
+
+    def new_state_buffer(self):
+        import torch
+
+        return torch.empty(self.state_bytes, dtype=torch.uint8, device="cuda")
+
+    def snapshot(self, buf):
+        lbm_snapshot(self._h, buf.data_ptr())
+        return buf
+
+    def restore(self, buf, t: int):
+        lbm_restore(self._h, buf.data_ptr(), t)
+
+    def adjoint_seed(self, dj_dphi):
+        lbm_adjoint_seed(self._h, self._field(dj_dphi))
+
+    def adjoint_step(self, state_buf):
+        lbm_adjoint_step(self._h, state_buf.data_ptr())
+
+    def adjoint_init(self, state0_buf) -> np.ndarray:
+        out = np.empty((self.ny, self.nx))
+        lbm_adjoint_init(self._h, state0_buf.data_ptr(), out)
+        return out
+
+    def adjoint_gravity(self) -> np.ndarray:
+        out = np.empty(2)
+        lbm_adjoint_gravity(self._h, out)
+        return out
 
 
 __all__ = ["Simulation", "LbmParams", "LbmError", "load", "params_struct", "torch_allocator",

@@ -51,6 +51,11 @@ struct lbm_handle {
   bool sg_node[9];
   double wa[4];
   double dv_r[2][2], dv_s[2], dv_c0;  // 16-bit deviation storage constants
+  // discrete adjoint (created on first use)
+  AdjBufs adj{};
+  bool have_adj = false;
+  double* gacc = nullptr;  // accumulated dJ/dG
+  bool init_u_zero = true; // the last lbm_init_fields had u = 0
 };
 
 static std::string g_create_error;
@@ -204,7 +209,7 @@ static Phys<T> make_phys(const lbm_handle* h) {
   P.beta4 = T(4.0 * h->beta);
   P.kappa = T(h->kappa);
   P.lam_coef = T(h->lam_coef);
-  P.n_delta = T(1e-3 * (Q.phiA - Q.phiB) / Q.width);
+  P.n_delta = T(5e-3 * (Q.phiA - Q.phiB) / Q.width);
   P.drho = T(h->drho);
   P.rhoB = T(Q.rhoB);
   P.rho_mean = T(0.5 * (Q.rhoA + Q.rhoB));
@@ -605,6 +610,7 @@ int lbm_create(const lbm_params* params, void* stream, const lbm_allocator* allo
 int lbm_init_fields(lbm_handle* h, const double* phi, const double* ux, const double* uy, const double* p) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   if (!phi) return fail(h, LBM_EINVAL, "phi is NULL");
+  h->init_u_zero = !ux && !uy;
   PFLBM_DISPATCH(h, do_init, h, phi, ux, uy, p);
 }
 
@@ -738,3 +744,151 @@ extern "C" int lbm_fields_noalloc(lbm_handle* h, int32_t which, double* out) {
   if (rc) return rc;
   PFLBM_DISPATCH(h, do_fields_noalloc, h, which, out, stage);
 }
+
+// ---------------------------------------------------------------------------
+// Snapshots and the discrete adjoint of the Allen-Cahn step
+// (pflbm_adjoint.cuh).  A snapshot is the f* set, the g* set and the five
+// history planes, byte for byte in the handle's layout.
+// ---------------------------------------------------------------------------
+static long long state_bytes(const lbm_handle* h) {
+  return 2 * h->pop_bytes + 5LL * h->plane * (long long)h->esize;
+}
+
+static int ensure_adjoint(lbm_handle* h) {
+  if (h->have_adj) return LBM_OK;
+  const size_t pl = (size_t)h->plane * h->esize;
+  void* planes = dev_alloc(h, 51 * pl);  // lf 9, lg 9, lh 5, lp9 9, lfp 9, lgp 9, phi 1
+  void* lext = dev_alloc(h, (size_t)(h->nx + 2) * (h->ny + 2) * h->esize);
+  const long long nblocks = (long long)((h->nx + ADJ_THREADS - 1) / ADJ_THREADS) * h->ny;
+  double* gpart = (double*)dev_alloc(h, (size_t)(2 * nblocks) * sizeof(double));
+  double* gacc = (double*)dev_alloc(h, 2 * sizeof(double));
+  if (!planes || !lext || !gpart || !gacc) {
+    for (void* q : {planes, lext, (void*)gpart, (void*)gacc}) dev_free(h, q);
+    return fail(h, LBM_ENOMEM, "adjoint work space (%zu bytes of planes)", 51 * pl);
+  }
+  unsigned char* b = static_cast<unsigned char*>(planes);
+  h->adj.lf = b;
+  h->adj.lg = b + 9 * pl;
+  h->adj.lh = b + 18 * pl;
+  h->adj.lp9 = b + 23 * pl;
+  h->adj.lfp = b + 32 * pl;
+  h->adj.lgp = b + 41 * pl;
+  h->adj.phi = b + 50 * pl;
+  h->adj.lext = lext;
+  h->adj.gpart = gpart;
+  h->gacc = gacc;
+  CUDA_TRY(h, cudaMemsetAsync(planes, 0, 51 * pl, h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(gacc, 0, 2 * sizeof(double), h->stream));
+  h->have_adj = true;
+  return LBM_OK;
+}
+
+static int adjoint_supported(lbm_handle* h) {
+  if (h->prm.phase_model != LBM_AC)
+    return fail(h, LBM_EUNSUPPORTED, "the adjoint covers the Allen-Cahn phase field only");
+  if (h->prec != LBM_FP64 && h->prec != LBM_FP32)
+    return fail(h, LBM_EUNSUPPORTED, "the adjoint needs FP64 or FP32 population storage");
+  return LBM_OK;
+}
+
+template <typename T>
+static int do_adjoint_seed(lbm_handle* h, const double* djdphi) {
+  const Phys<T> P = make_phys<T>(h);
+  int rc = ensure_stage(h, 1);
+  if (rc) return rc;
+  const long long N = (long long)h->nx * h->ny;
+  CUDA_TRY(h, cudaMemcpyAsync(h->dstage, djdphi, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, launch_adjoint_seed<T>(P, h->dstage, h->adj, h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->gacc, 0, 2 * sizeof(double), h->stream));
+  return LBM_OK;
+}
+
+template <typename T>
+static int do_adjoint_step(lbm_handle* h, const void* state) {
+  const Phys<T> P = make_phys<T>(h);
+  CUDA_TRY(h, launch_adjoint_step<T>(P, state, h->pop_bytes, h->adj, h->gacc, false, h->stream));
+  return LBM_OK;
+}
+
+template <typename T>
+static int do_adjoint_init(lbm_handle* h, const void* state0, double* out) {
+  const Phys<T> P = make_phys<T>(h);
+  int rc = ensure_stage(h, 1);
+  if (rc) return rc;
+  CUDA_TRY(h, launch_adjoint_step<T>(P, state0, h->pop_bytes, h->adj, h->gacc, true, h->stream));
+  CUDA_TRY(h, launch_adjoint_init<T>(P, h->adj, h->dstage, h->stream));
+  const long long N = (long long)h->nx * h->ny;
+  CUDA_TRY(h, cudaMemcpyAsync(out, h->dstage, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return check_device_flag(h);
+}
+
+extern "C" {
+
+int64_t lbm_state_bytes(const lbm_handle* h) { return h ? state_bytes(h) : 0; }
+
+int lbm_snapshot(lbm_handle* h, void* dst) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!dst) return fail(h, LBM_EINVAL, "dst is NULL");
+  unsigned char* d = static_cast<unsigned char*>(dst);
+  CUDA_TRY(h, cudaMemcpyAsync(d, h->pops[0][h->cur], h->pop_bytes, cudaMemcpyDeviceToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(d + h->pop_bytes, h->pops[1][h->cur], h->pop_bytes, cudaMemcpyDeviceToDevice,
+                              h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(d + 2 * h->pop_bytes, h->hist, 5 * h->plane * h->esize, cudaMemcpyDeviceToDevice,
+                              h->stream));
+  return LBM_OK;
+}
+
+int lbm_restore(lbm_handle* h, const void* src, int64_t t) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!src || t < 0) return fail(h, LBM_EINVAL, "src is NULL or t < 0");
+  const unsigned char* s = static_cast<const unsigned char*>(src);
+  CUDA_TRY(h, cudaMemcpyAsync(h->pops[0][h->cur], s, h->pop_bytes, cudaMemcpyDeviceToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->pops[1][h->cur], s + h->pop_bytes, h->pop_bytes, cudaMemcpyDeviceToDevice,
+                              h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->hist, s + 2 * h->pop_bytes, 5 * h->plane * h->esize, cudaMemcpyDeviceToDevice,
+                              h->stream));
+  h->t = t;
+  return LBM_OK;
+}
+
+int lbm_adjoint_seed(lbm_handle* h, const double* dJ_dphi) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!dJ_dphi) return fail(h, LBM_EINVAL, "dJ_dphi is NULL");
+  int rc = adjoint_supported(h);
+  if (!rc) rc = ensure_adjoint(h);
+  if (rc) return rc;
+  return h->prec == LBM_FP64 ? do_adjoint_seed<double>(h, dJ_dphi) : do_adjoint_seed<float>(h, dJ_dphi);
+}
+
+int lbm_adjoint_step(lbm_handle* h, const void* state) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!state) return fail(h, LBM_EINVAL, "state is NULL");
+  int rc = adjoint_supported(h);
+  if (rc) return rc;
+  if (!h->have_adj) return fail(h, LBM_EINVAL, "lbm_adjoint_seed has not been called");
+  return h->prec == LBM_FP64 ? do_adjoint_step<double>(h, state) : do_adjoint_step<float>(h, state);
+}
+
+int lbm_adjoint_init(lbm_handle* h, const void* state0, double* dJ_dphi0) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!state0 || !dJ_dphi0) return fail(h, LBM_EINVAL, "state0 or dJ_dphi0 is NULL");
+  int rc = adjoint_supported(h);
+  if (rc) return rc;
+  if (!h->have_adj) return fail(h, LBM_EINVAL, "lbm_adjoint_seed has not been called");
+  if (!h->init_u_zero)
+    return fail(h, LBM_EUNSUPPORTED, "lbm_adjoint_init differentiates lbm_init_fields with u = 0 only");
+  return h->prec == LBM_FP64 ? do_adjoint_init<double>(h, state0, dJ_dphi0)
+                             : do_adjoint_init<float>(h, state0, dJ_dphi0);
+}
+
+int lbm_adjoint_gravity(lbm_handle* h, double* dJ_dG) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!dJ_dG) return fail(h, LBM_EINVAL, "dJ_dG is NULL");
+  if (!h->have_adj) return fail(h, LBM_EINVAL, "lbm_adjoint_seed has not been called");
+  CUDA_TRY(h, cudaMemcpyAsync(dJ_dG, h->gacc, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return check_device_flag(h);
+}
+
+}  // extern "C"

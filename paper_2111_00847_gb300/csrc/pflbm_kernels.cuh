@@ -76,7 +76,7 @@ struct Phys {
   int gravity_mode, visc_inverse, sg7_node, sg8_node;
   T phiA, phiB, phibar, inv_dphi;
   T beta4, kappa, lam_coef;  // 4 beta, k, sqrt(2 beta / k)   (Eqs. (3), (5), (8))
-  T n_delta;                 // floor of |grad phi| in n = grad phi / |grad phi|
+  T n_delta;                 // regularisation of |grad phi| in n = grad phi / |grad phi|
   T drho, rhoB, rho_mean;    // d rho / d phi, rho_B, (rho_A + rho_B)/2
   T mob_drho;                // (d rho/d phi) M_phi, zero for the original model
   T muA, muB, inuA, inuB;    // mu_A, mu_B, 1/nu_A, 1/nu_B
@@ -151,18 +151,19 @@ struct Bufs {
 
 __host__ __device__ constexpr int slot_of(int r) { return (r + 2 * RING) & (RING - 1); }
 
-// Division and the normal's 1/max(|grad phi|, delta): IEEE in FP64 (the
-// path held to 1e-12 against the oracle), hardware approximations in FP32
-// (<= 2 ulp, far inside the FP32 tolerance) where they save the slow path
-// of an IEEE divide.
+// Division and the normal's 1/(|grad phi|^4 + delta^4)^(1/4): IEEE in FP64
+// (the path held to 1e-12 against the oracle), hardware approximations in
+// FP32 (<= 2 ulp each, far inside the FP32 tolerance) where they save the
+// slow path of an IEEE divide or square root.
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double inv_floor_norm(double g2, double delta) {
-  const double gm = sqrt(g2);
-  return 1.0 / (gm > delta ? gm : delta);
+__device__ __forceinline__ double inv_soft_norm(double g2, double delta) {
+  const double d2 = delta * delta;
+  return 1.0 / sqrt(sqrt(g2 * g2 + d2 * d2));
 }
-__device__ __forceinline__ float inv_floor_norm(float g2, float delta) {
-  return rsqrtf(fmaxf(g2, delta * delta));
+__device__ __forceinline__ float inv_soft_norm(float g2, float delta) {
+  const float d2 = delta * delta;
+  return rsqrtf(sqrtf(g2 * g2 + d2 * d2));
 }
 
 // element k of a set of NP row-interleaved planes at node (x, y)
@@ -344,11 +345,12 @@ __device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, 
                   (((phi9[5] - phi) + (phi9[7] - phi)) + ((phi9[6] - phi) + (phi9[8] - phi))) * T(1.0 / 6.0);
     // chemical potential, Eq. (5)
     mu = P.beta4 * (phi - P.phiA) * (phi - P.phiB) * (phi - P.phibar) - P.kappa * lap;
-    // conservative AC flux, Eqs. (7)-(8), n = grad phi / max(|grad phi|, delta_n)
-    // (delta_n = 1e-3 dphi / W: the unit normal across the interface, and a
-    // Lipschitz function of grad phi in the bulk where |grad phi| -> 0)
+    // conservative AC flux, Eqs. (7)-(8), n = grad phi / (|grad phi|^4 + delta_n^4)^(1/4)
+    // (delta_n = 5e-3 dphi / W: the unit normal across the interface, and a
+    // smooth function of grad phi with slope about 1/delta_n in the bulk,
+    // where |grad phi| -> 0)
     lam = P.lam_coef * (P.phiA - phi) * (phi - P.phiB);
-    const T inv = inv_floor_norm(gx * gx + gy * gy, P.n_delta);
+    const T inv = inv_soft_norm(gx * gx + gy * gy, P.n_delta);
     nnx = gx * inv;
     nny = gy * inv;
     Dx = gx - lam * nnx;

@@ -99,6 +99,50 @@ cudaError_t launch_diag(const Phys<T>& P, const T* macro, const T* phi_prev, dou
   return cudaGetLastError();
 }
 
+// One adjoint step (or, with hist_only, the adjoint of the history set-up at
+// t = 0 without the reverse streaming).  state: snapshot of the step's input
+// state (f* set, g* set of pop_bytes each, then the 5 history planes).
+template <typename T>
+cudaError_t launch_adjoint_step(const Phys<T>& P, const void* state, long long pop_bytes, const AdjBufs& A,
+                                double* gacc, bool hist_only, cudaStream_t s) {
+  const T* fin = static_cast<const T*>(state);
+  const T* gin = reinterpret_cast<const T*>(static_cast<const unsigned char*>(state) + pop_bytes);
+  const T* hist = reinterpret_cast<const T*>(static_cast<const unsigned char*>(state) + 2 * pop_bytes);
+  T* phi = static_cast<T*>(A.phi);
+  T* lext = static_cast<T*>(A.lext);
+  const dim3 grid((P.nx + ADJ_THREADS - 1) / ADJ_THREADS, P.ny);
+  k_adj_phi<T><<<grid, ADJ_THREADS, 0, s>>>(P, fin, phi);
+  k_adj_node<T><<<grid, ADJ_THREADS, 0, s>>>(P, fin, gin, hist, phi, static_cast<const T*>(A.lf),
+                                             static_cast<const T*>(A.lg), static_cast<T*>(A.lh),
+                                             static_cast<T*>(A.lp9), static_cast<T*>(A.lfp),
+                                             static_cast<T*>(A.lgp), A.gpart, hist_only ? 1 : 0);
+  const int ex = P.nx + 2 * P.wall_x, ey = P.ny + 2 * P.wall_y;
+  k_adj_gather<T><<<dim3((ex + ADJ_THREADS - 1) / ADJ_THREADS, ey), ADJ_THREADS, 0, s>>>(
+      P, static_cast<const T*>(A.lp9), lext);
+  if (P.wall_y) k_adj_fold_y<T><<<(ex + ADJ_THREADS - 1) / ADJ_THREADS, ADJ_THREADS, 0, s>>>(P, phi, lext);
+  if (P.wall_x) k_adj_fold_x<T><<<(P.ny + ADJ_THREADS - 1) / ADJ_THREADS, ADJ_THREADS, 0, s>>>(P, phi, lext);
+  if (!hist_only)
+    k_adj_stream<T><<<grid, ADJ_THREADS, 0, s>>>(P, static_cast<const T*>(A.lfp), static_cast<const T*>(A.lgp),
+                                                 lext, static_cast<T*>(A.lf), static_cast<T*>(A.lg));
+  k_adj_reduce<T><<<1, 256, 0, s>>>(A.gpart, (long long)grid.x * grid.y, gacc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_adjoint_seed(const Phys<T>& P, const double* djdphi, const AdjBufs& A, cudaStream_t s) {
+  const dim3 grid((P.nx + ADJ_THREADS - 1) / ADJ_THREADS, P.ny);
+  k_adj_seed<T><<<grid, ADJ_THREADS, 0, s>>>(P, djdphi, static_cast<T*>(A.lf), static_cast<T*>(A.lg),
+                                             static_cast<T*>(A.lh));
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_adjoint_init(const Phys<T>& P, const AdjBufs& A, double* out, cudaStream_t s) {
+  const dim3 grid((P.nx + ADJ_THREADS - 1) / ADJ_THREADS, P.ny);
+  k_adj_init<T><<<grid, ADJ_THREADS, 0, s>>>(P, static_cast<const T*>(A.lf), static_cast<const T*>(A.lext), out);
+  return cudaGetLastError();
+}
+
 // the codec-typed wrappers of one storage codec
 #define PFLBM_INSTANTIATE_CODEC(C)                                                                  \
   template cudaError_t launch_march<C>(int, int, const Phys<C::value_t>&, const Bufs<C::value_t>&,  \
@@ -123,6 +167,11 @@ cudaError_t launch_diag(const Phys<T>& P, const T* macro, const T* phi_prev, dou
   template cudaError_t launch_import<T>(const Phys<T>&, const double*, T*, int, int, double,      \
                                         cudaStream_t);                                             \
   template cudaError_t launch_diag<T>(const Phys<T>&, const T*, const T*, double*, int, double*,  \
-                                      cudaStream_t);
+                                      cudaStream_t);                                             \
+  template cudaError_t launch_adjoint_step<T>(const Phys<T>&, const void*, long long, const AdjBufs&, \
+                                              double*, bool, cudaStream_t);                       \
+  template cudaError_t launch_adjoint_seed<T>(const Phys<T>&, const double*, const AdjBufs&,      \
+                                              cudaStream_t);                                      \
+  template cudaError_t launch_adjoint_init<T>(const Phys<T>&, const AdjBufs&, double*, cudaStream_t);
 
 }  // namespace pflbm

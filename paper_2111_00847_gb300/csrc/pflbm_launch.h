@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "pflbm_kernels.cuh"
+#include "pflbm_adjoint.cuh"
 
 namespace pflbm {
 
@@ -42,5 +43,13 @@ cudaError_t launch_import(const Phys<T>& P, const double* in, T* out, int NP, in
 template <typename T>
 cudaError_t launch_diag(const Phys<T>& P, const T* macro, const T* phi_prev, double* partial,
                         int nparts, double* out, cudaStream_t s);
+// discrete adjoint of the Allen-Cahn step (pflbm_adjoint.cuh), plain storage
+template <typename T>
+cudaError_t launch_adjoint_step(const Phys<T>& P, const void* state, long long pop_bytes, const AdjBufs& A,
+                                double* gacc, bool hist_only, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adjoint_seed(const Phys<T>& P, const double* djdphi, const AdjBufs& A, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adjoint_init(const Phys<T>& P, const AdjBufs& A, double* out, cudaStream_t s);
 
 }  // namespace pflbm
