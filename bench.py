@@ -59,6 +59,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-storage-compare", action="store_true",
                     help="skip timing the 16-bit deviation storage beside FP32")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip timing the adjoint against the forward pass")
+    ap.add_argument("--adjoint-steps", type=int, default=400)
+    ap.add_argument("--adjoint-precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="time only the adjoint against the forward pass (profiling)")
     return ap.parse_args()
 
 
@@ -212,6 +218,41 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def adjoint_timing(args, torch):
+    """Adjoint/forward time ratio on the adjoint workload (512 x 2048 RTI,
+    Atwood 0.5, Re 1000, 8 seeded modes; checkpoints every 100 steps;
+    J = phi-weighted vertical centroid), over a shorter horizon than its
+    2000 steps.  Wall time with the device synchronised on both sides of the
+    forward rollout and of the backward pass (recomputation included); the
+    first of two passes warms allocations and kernels up."""
+    from paper_2111_00847_gb300.adjoint import centroid_y, interface_phi0, rollout
+
+    prec = W.PREC_FP64 if args.adjoint_precision == "fp64" else W.PREC_FP32
+    case = W.rti_adjoint(precision=prec)
+    prm = case.params
+    every = 100
+    out = {}
+    for _ in range(2):
+        a = torch.tensor(case.notes["a"], dtype=torch.float64, requires_grad=True)
+        G = torch.tensor([prm.gx, prm.gy], dtype=torch.float64, requires_grad=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        phiN = rollout(interface_phi0(a, prm.nx, prm.ny, prm.width, prm.phiA, prm.phiB), G, prm,
+                       args.adjoint_steps, every)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        centroid_y(phiN).backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        out = {"workload": "rti_adjoint_512x2048_atwood0.5_re1000_8modes",
+               "precision": args.adjoint_precision, "steps": args.adjoint_steps, "checkpoint_every": every,
+               "forward_ms_per_step": (t1 - t0) / args.adjoint_steps * 1e3,
+               "backward_ms_per_step": (t2 - t1) / args.adjoint_steps * 1e3,
+               "ratio": (t2 - t1) / (t1 - t0),
+               "what": "backward = checkpoint recomputation + adjoint steps; wall time, device synchronised"}
+    return out
+
+
 # ---------------------------------------------------------------------------
 def main():
     args = parse()
@@ -228,6 +269,14 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.adjoint_only:
+        import __graft_entry__
+
+        __graft_entry__.build()
+        if rank == 0:
+            print(json.dumps({"metric": "adjoint/forward time ratio", "adjoint": adjoint_timing(args, torch)}),
+                  flush=True)
+        return
 
     import __graft_entry__
 
@@ -326,6 +375,10 @@ def main():
                              "ms_per_step": ms16 / args.steps, "roofline": roof16, "clocks": clk16,
                              "gain_vs_fp32": ms / ms16}
 
+    adjoint = None
+    if rank == 0 and not args.no_adjoint:
+        adjoint = adjoint_timing(args, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(case, args.cpu_seconds)
@@ -340,7 +393,8 @@ def main():
                            "replicas": world, "parallelism": f"replicas{world}",
                            "l2": f"inputs larger than L2 (device state {state_gb:.1f} GB)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": args.steps, "clocks": clk, "storage_variants": storage}
+                "gpu_launches": args.steps, "clocks": clk, "storage_variants": storage,
+                "adjoint": adjoint}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

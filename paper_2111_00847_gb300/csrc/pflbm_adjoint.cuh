@@ -109,9 +109,9 @@ __device__ __forceinline__ void mtmul(const T v[9], T o[9]) {
   o[8] = r1 + qx - qy - v[8];
 }
 
-// Squared norms of the rows of M: M^{-1} = M^T diag(1 / |row k|^2).
-__device__ __forceinline__ double row_norm2(int k) {
-  const double n[9] = {9, 36, 36, 6, 12, 6, 12, 4, 4};
+// Reciprocal squared norms of the rows of M: M^{-1} = M^T diag(1 / |row k|^2).
+__device__ __forceinline__ double inv_row_norm2(int k) {
+  const double n[9] = {1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 6, 1.0 / 12, 1.0 / 6, 1.0 / 12, 0.25, 0.25};
   return n[k];
 }
 
@@ -137,9 +137,7 @@ __device__ void node_adjoint(const Phys<T>& P, const T phi9[9], const T f[9], co
   const T mu = P.beta4 * pa * pb * pc - P.kappa * lap;
   const T lam = P.lam_coef * (P.phiA - phi) * pb;
   const T g2 = gx * gx + gy * gy;
-  const T d2 = P.n_delta * P.n_delta;
-  const T S = g2 * g2 + d2 * d2;
-  const T inv = T(1) / sqrt(sqrt(S));  // r = S^(-1/4)
+  const T inv = inv_soft_norm(g2, P.n_delta);  // r = (g2^2 + delta^4)^(-1/4)
   const T nx_ = gx * inv, ny_ = gy * inv;
   const T Dx = gx - lam * nx_, Dy = gy - lam * ny_;
   const T rho = P.drho * pb + P.rhoB;
@@ -152,7 +150,7 @@ __device__ void node_adjoint(const Phys<T>& P, const T phi9[9], const T f[9], co
   const T g13 = g[1] - g[3], g24 = g[2] - g[4];
   const T gdx = (g[5] - g[7]) + (g[8] - g[6]);
   const T gdy = (g[5] - g[7]) + (g[6] - g[8]);
-  const T irho = T(1) / rho;
+  const T irho = fdiv(T(1), rho);
   const T nxu = (g13 + gdx) + T(0.5) * Fx, nyu = (g24 + gdy) + T(0.5) * Fy;
   const T u = nxu * irho, v = nyu * irho;
   const T um = u * mcx + v * mcy, cA = u * mcx - v * mcy, cB = u * mcy + v * mcx;
@@ -203,7 +201,7 @@ __device__ void node_adjoint(const Phys<T>& P, const T phi9[9], const T f[9], co
     T leq[9], lsrc[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      const T lm = a[k] / T(row_norm2(k));
+      const T lm = a[k] * T(inv_row_norm2(k));
       lmf[k] = (T(1) - P.sf[k]) * lm;
       leq[k] = P.sf[k] * lm;
       lsrc[k] = P.hf[k] * lm;
@@ -227,7 +225,7 @@ __device__ void node_adjoint(const Phys<T>& P, const T phi9[9], const T f[9], co
     mmul(lgs, a);
     T lm[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) lm[k] = a[k] / T(row_norm2(k));
+    for (int k = 0; k < 9; ++k) lm[k] = a[k] * T(inv_row_norm2(k));
     T s[9];
 #pragma unroll
     for (int k = 0; k < 7; ++k) s[k] = P.sg[k];

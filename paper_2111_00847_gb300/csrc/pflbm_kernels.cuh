@@ -162,8 +162,10 @@ __device__ __forceinline__ double inv_soft_norm(double g2, double delta) {
   return 1.0 / sqrt(sqrt(g2 * g2 + d2 * d2));
 }
 __device__ __forceinline__ float inv_soft_norm(float g2, float delta) {
+  // S^(-1/4) = y * y^(-1/2) with y = S^(-1/2): two reciprocal square roots
   const float d2 = delta * delta;
-  return rsqrtf(sqrtf(g2 * g2 + d2 * d2));
+  const float y = rsqrtf(g2 * g2 + d2 * d2);
+  return y * rsqrtf(y);
 }
 
 // element k of a set of NP row-interleaved planes at node (x, y)
