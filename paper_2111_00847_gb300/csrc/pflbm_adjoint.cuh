@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(ADJ_THREADS)
                T* __restrict__ lp9, T* __restrict__ lfp, T* __restrict__ lgp, double* __restrict__ gpart,
                int hist_only) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-  double gxs = 0.0, gys = 0.0;
+  T gxs = T(0), gys = T(0);
   if (x < P.nx) {
     T phi9[9], f[9], g[9], h[5], lfs[9], lgs[9], lhn[5];
     const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -439,10 +439,11 @@ __global__ void __launch_bounds__(ADJ_THREADS)
     }
 #pragma unroll
     for (int k = 0; k < 5; ++k) lh[ix(P, 5, k, x, y)] = lho[k];
-    gxs = double(lGx);
-    gys = double(lGy);
+    gxs = lGx;
+    gys = lGy;
   }
-  // block sums of dJ/dG
+  // block sums of dJ/dG: within a warp in the arithmetic type, across warps
+  // and blocks in double
   __shared__ double red[ADJ_THREADS / 32][2];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -451,8 +452,8 @@ __global__ void __launch_bounds__(ADJ_THREADS)
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
-    red[wid][0] = gxs;
-    red[wid][1] = gys;
+    red[wid][0] = double(gxs);
+    red[wid][1] = double(gys);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
