@@ -856,7 +856,9 @@ struct Seg {
 };
 // Rings: f rows y-1 .. y+2 are live while row y is processed (pulls of row y,
 // phi of row y+1) and DF more rows are in flight; g rows y-1 .. y+1 are live
-// and DG more are in flight.
+// and DG more are in flight.  SLIM: the pulled f of row y is kept in
+// registers from phi's pass over that row, so f row y-1 is not needed and
+// the f ring is one row shorter.
 // phi ring of the TMA step: rows y-2 .. y+1 can be in use at once (slower
 // threads of the previous march step read y-2 .. y while row y+1 is formed)
 constexpr int TRING = 4;
@@ -864,11 +866,11 @@ __host__ __device__ constexpr int tslot(int r) { return (r + 2 * TRING) & (TRING
 
 // A staged row slot holds the segment of each of the nine planes: plane 0
 // (SEG elements of B0 bytes) then planes 1..8 (SEG elements of BI bytes).
-template <class C, int TBX, int DF, int DG>
+template <class C, int TBX, int DF, int DG, bool SLIM = false>
 struct TmaLayout {
   using T = typename C::value_t;
   static constexpr int SEG = Seg<TBX>::value;
-  static constexpr int RF = 4 + DF, RG = 3 + DG;
+  static constexpr int RF = (SLIM ? 3 : 4) + DF, RG = 3 + DG;
   static constexpr size_t P0 = (size_t)SEG * C::B0;   // bytes of plane 0's segment
   static constexpr size_t PI = (size_t)SEG * C::BI;   // bytes of each other plane's segment
   static constexpr size_t SLOT = P0 + 8 * PI;
@@ -971,8 +973,10 @@ __device__ __forceinline__ void pull_staged(const unsigned char* rm, const unsig
 // ahead of need (f, g), resident threads per SM it is compiled for
 // (registers), and whether the f pulled for phi of row y+1 is kept in
 // registers for that row's collision instead of being pulled again.
-//   FP32: 160 columns, one row ahead, 4 blocks (20 warps) per SM: shared
-//         memory (56 KB a block) is the occupancy limit.
+//   FP32: 160 columns, f one row ahead, g two, 4 blocks (20 warps) per SM:
+//         shared memory (56 KB a block) is the occupancy limit.  f is kept
+//         from phi's pass (SLIM), and the f slot that frees holds the extra g
+//         row.
 //   FP64: 160 columns, one row ahead, one block per SM (registers).
 //   16-bit deviations: 128 columns, two rows ahead, 6 blocks (24 warps) per
 //         SM; the rows are 44 % smaller, so more blocks fit, and keeping f
@@ -984,13 +988,16 @@ __device__ __forceinline__ void pull_staged(const unsigned char* rm, const unsig
 // issued from every warp 27-29.  Keeping f in FP32 too, which frees the f
 // ring's row y-1 and lets f be staged two rows ahead in the same shared
 // memory (the segment's first phi row then pulled from global memory):
-// FP32 30.6 (unchanged), FP16 deviations 32.3 (register spills).
+// FP32 30.6 (unchanged), FP16 deviations 32.3 (register spills); the same
+// ring with g staged two rows ahead instead: FP32 32.0.
 template <class C>
 struct TmaCfg {
   static constexpr int TBX = C::dev ? 128 : 160;
-  static constexpr int DF = C::dev ? 2 : 1, DG = C::dev ? 2 : 1;
+  static constexpr bool fp32 = !C::dev && sizeof(typename C::value_t) == 4;
+  static constexpr int DF = C::dev ? 2 : 1, DG = (C::dev || fp32) ? 2 : 1;
   static constexpr int threads = C::dev ? 768 : (sizeof(typename C::value_t) == 4 ? 640 : 256);
-  static constexpr bool keep_f = C::dev;
+  static constexpr bool keep_f = C::dev || fp32;
+  static constexpr bool slim = fp32;
 };
 
 template <class C, bool UR>
@@ -999,7 +1006,8 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
   using T = typename C::value_t;
   constexpr int TBX = TmaCfg<C>::TBX, DF = TmaCfg<C>::DF, DG = TmaCfg<C>::DG;
   constexpr bool FK = TmaCfg<C>::keep_f;
-  using L = TmaLayout<C, TBX, DF, DG>;
+  constexpr bool SLIM = TmaCfg<C>::slim;  // (implies FK) the f ring starts at row y0 - 1
+  using L = TmaLayout<C, TBX, DF, DG, SLIM>;
   constexpr int SEG = L::SEG, RF = L::RF, RG = L::RG;
   constexpr int FS = (int)L::SLOT;  // bytes per row slot
   extern __shared__ __align__(128) unsigned char smem[];
@@ -1017,7 +1025,7 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
   const bool active = tid < w;
   const int x = x0 + tid;
   const bool wx = P.wall_x != 0, wy = P.wall_y != 0;
-  const int fbase = y0 - 2, gbase = y0 - 1;  // first staged f / g row
+  const int fbase = y0 - (SLIM ? 1 : 2), gbase = y0 - 1;  // first staged f / g row
   // bytes copied per plane segment: [x0 - XPAD, x0 + w + XPAD) rounded up to 16
   const uint32_t seg0 = (uint32_t)((((w + 2 * XPAD) * C::B0 + 15) / 16) * 16);
   const uint32_t segI = (uint32_t)((((w + 2 * XPAD) * C::BI + 15) / 16) * 16);
@@ -1108,6 +1116,29 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
     }
   };
   auto phi_row = [&](int r) { phi_row_at(r, fslot(r - 1), fslot(r), fslot(r + 1), r == y0); };
+  // SLIM: phi of row y0 - 1 (in the domain or wrapped) from pulls of the
+  // global planes, since its f rows are not staged.
+  auto phi_row_global = [&](int r) {
+    const int rr = wrap_row(r);
+    T* dst = sp + tslot(r) * (TBX + 2);
+    if (!active) return;
+    const T ph = phi_at<C, MODE_STEP>(P, B, x, rr);
+    dst[tid + 1] = ph;
+    if (tid == 0) {
+      T hv;
+      if (x0 > 0) hv = phi_at<C, MODE_STEP>(P, B, x0 - 1, rr);
+      else if (!wx) hv = phi_at<C, MODE_STEP>(P, B, nx - 1, rr);
+      else hv = wall_ghost(P, SIDE_LEFT, ph, phi_at<C, MODE_STEP>(P, B, 1, rr));
+      dst[0] = hv;
+    }
+    if (tid == w - 1) {
+      T hv;
+      if (x0 + w < nx) hv = phi_at<C, MODE_STEP>(P, B, x0 + w, rr);
+      else if (!wx) hv = phi_at<C, MODE_STEP>(P, B, 0, rr);
+      else hv = wall_ghost(P, SIDE_RIGHT, ph, phi_at<C, MODE_STEP>(P, B, nx - 2, rr));
+      dst[w + 1] = hv;
+    }
+  };
   auto ghost_row = [&](int rg, int r1, int r2, int side) {
     T* d = sp + tslot(rg) * (TBX + 2);
     const T* a = sp + tslot(r1) * (TBX + 2);
@@ -1117,7 +1148,7 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
 
   bool ok = true;
   // ---------------------------------------------------------------- prologue
-  // f rows y0-2 .. y0+1+DF and g rows y0-1 .. y0+DG in flight; phi of rows
+  // f rows fbase .. y0+1+DF and g rows y0-1 .. y0+DG in flight; phi of rows
   // y0-1 and y0 (and of row 1 when the segment starts at a bottom wall, so
   // that the ghost row below it can be formed before the march).
   const bool bottom = wy && y0 == 0;
@@ -1127,8 +1158,12 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
   }
   for (int r = fbase; r <= min(y0 + (bottom ? 2 : 1), f_last); ++r) ok = wait_f(r) && ok;
   for (int r = gbase; r <= min(y0, g_last); ++r) ok = wait_g(r) && ok;
-  for (int r = y0 - 1; r <= y0 + (bottom ? 1 : 0); ++r)
-    if ((r >= 0 && r < ny) || !wy) phi_row(r);
+  for (int r = y0 - 1; r <= y0 + (bottom ? 1 : 0); ++r) {
+    if ((r >= 0 && r < ny) || !wy) {
+      if (SLIM && r == y0 - 1) phi_row_global(r);
+      else phi_row(r);
+    }
+  }
   bool failed = __syncthreads_or(!ok);
   if (!failed && bottom) {
     ghost_row(-1, 0, 1, SIDE_BOTTOM);
@@ -1142,13 +1177,14 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
   }
 
   // ---------------------------------------------------------------- march
-  // Ring positions advance by one slot per row: f slot of row y-1 and g slot
+  // Ring positions advance by one slot per row: f slot of row y and g slot
   // of row y-1, and slot + phase parity of the rows waited for (f row y+2,
   // g row y+1), kept as counters instead of modulo arithmetic.
   auto next = [](int s, int R) { return s + 1 == R ? 0 : s + 1; };
   auto add = [](int s, int k, int R) { return s + k >= R ? s + k - R : s + k; };
-  int fA = 1 % RF, gA = 0;                   // rows y0-1 (f: local 1, g: local 0)
-  int fW = 4 % RF, fWp = (4 / RF) & 1;       // f row y0+2 (local 4)
+  constexpr int LF0 = SLIM ? 1 : 2;                        // local index of f row y0
+  int fR0 = LF0 % RF, gA = 0;                              // f row y0, g row y0-1
+  int fW = (LF0 + 2) % RF, fWp = ((LF0 + 2) / RF) & 1;     // f row y0+2
   int gW = 2 % RG, gWp = (2 / RG) & 1;       // g row y0+1 (local 2)
   for (int y = y0; y < y1 && !failed; ++y) {
     ok = true;
@@ -1159,19 +1195,19 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
 #pragma unroll
       for (int i = 0; i < 9; ++i) f[i] = fnext[i];
     }
-    const unsigned char* f_m = sf + fA * FS;                 // f row y-1
-    const unsigned char* f_0 = sf + add(fA, 1, RF) * FS;     // f row y
-    const unsigned char* f_p = sf + add(fA, 2, RF) * FS;     // f row y+1
+    const unsigned char* f_m = sf + add(fR0, RF - 1, RF) * FS;  // f row y-1 (not SLIM)
+    const unsigned char* f_0 = sf + fR0 * FS;                   // f row y
+    const unsigned char* f_p = sf + add(fR0, 1, RF) * FS;       // f row y+1
     // phi of row y+1 (a ghost row above a top wall)
     const int r1 = y + 1;
-    if (r1 < ny || !wy) phi_row_at(r1, f_0, f_p, sf + add(fA, 3, RF) * FS, true);
+    if (r1 < ny || !wy) phi_row_at(r1, f_0, f_p, sf + add(fR0, 2, RF) * FS, true);
     else if (r1 == ny) ghost_row(ny, ny - 1, ny - 2, SIDE_TOP);  // rows ny-1, ny-2 ready since the last barrier
     failed = __syncthreads_or(!ok);
     if (failed) break;
     if (tid == 0) {
       fence_proxy_async_smem();
       if (y + 2 + DF <= f_last) {
-        const int sl = add(fA, 3 + DF, RF);
+        const int sl = add(fR0, 2 + DF, RF);
         stage(B.fin, sf + sl * FS, &barF[sl], y + 2 + DF);
       }
       if (y + 1 + DG <= g_last) {
@@ -1217,7 +1253,7 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
     }
 #pragma unroll
     for (int k = 0; k < 5; ++k) h[k] = hn[k];
-    fA = next(fA, RF);
+    fR0 = next(fR0, RF);
     gA = next(gA, RG);
     fW = next(fW, RF);
     if (fW == 0) fWp ^= 1;

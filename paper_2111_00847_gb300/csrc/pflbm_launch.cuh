@@ -30,7 +30,7 @@ template <class C, bool UR>
 static cudaError_t launch_tma_variant(const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B,
                                       int* err, cudaStream_t s) {
   using G = TmaCfg<C>;
-  using L = TmaLayout<C, G::TBX, G::DF, G::DG>;
+  using L = TmaLayout<C, G::TBX, G::DF, G::DG, G::slim>;
   // per function and device; cheap next to a step
   cudaError_t e = cudaFuncSetAttribute(k_step_tma<C, UR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L::bytes);
