@@ -218,6 +218,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks_of(x: float, world: int, dist, device) -> float:
+    """The largest of the ranks' values of x (one all-reduce; the job's time
+    is its slowest replica's)."""
+    if world == 1:
+        return x
+    import torch
+
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world: int, nodes_per_rank: int, steps: int, seconds: float) -> float:
+    """Lattice updates of all replicas per second of the slowest one, / 1e6."""
+    return world * nodes_per_rank * steps / seconds / 1e6
+
+
 def adjoint_timing(args, torch):
     """Adjoint/forward time ratio on the adjoint workload (512 x 2048 RTI,
     Atwood 0.5, Re 1000, 8 seeded modes; checkpoints every 100 steps;
@@ -296,11 +313,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_of(x, world, dist, dev)
 
     stream = torch.cuda.current_stream(dev)
     peak, peak_src = measured_peak()
@@ -337,7 +350,7 @@ def main():
     # ---- device-resident timed region
     sim, ms, roofline, clk = timed_steps(case.params, args.precision, bytes_per_lu)
     sec = ms / 1e3
-    value = world * N * args.steps / sec / 1e6
+    value = whole_job_mlups(world, N, args.steps, sec)
 
     # ---- end to end through the public API, host buffers, copies inside
     e2e = None
