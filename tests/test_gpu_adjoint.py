@@ -194,3 +194,46 @@ def test_fp32_adjoint_tracks_fp64(pk, capsys):
               f"forward + backward {t64:.2f} s (FP64), {t32:.2f} s (FP32)")
     assert e <= 5e-3
     assert gy32 == pytest.approx(gy64, rel=1e-3)
+
+
+def test_snapshot_restore_continues_bit_exactly(pk):
+    """A state restored from a snapshot steps on exactly as the run it was
+    taken from."""
+    case = W.noisy_drop(96, 80, precision=W.PREC_FP32, walls="all", theta=(60, 120, 75, 105),
+                        gravity=(W.GRAV_RHO, 0.0, -1e-5))
+    sim = pk.Simulation(case.params)
+    sim.init_fields(case.phi)
+    sim.step(10)
+    buf = sim.snapshot(sim.new_state_buffer())
+    sim.step(20)
+    ref = [sim.fields(w) for w in (pk.LBM_F_POP, pk.LBM_G_POP, pk.LBM_HIST)]
+    sim.step(5)
+    sim.restore(buf, 10)
+    assert sim.t == 10
+    sim.step(20)
+    for a, w in zip(ref, (pk.LBM_F_POP, pk.LBM_G_POP, pk.LBM_HIST)):
+        assert np.array_equal(a, sim.fields(w))
+
+
+def test_adjoint_rejects_what_it_does_not_cover(pk):
+    """Cahn-Hilliard, 16-bit storage and an initial velocity are refused with
+    LBM_EUNSUPPORTED; an adjoint step before the seed with LBM_EINVAL."""
+    dj = np.zeros((40, 48))
+    for prm in (W.noisy_drop(48, 40, precision=W.PREC_FP64, model=W.MODEL_CH).params,
+                W.noisy_drop(48, 40, precision=W.PREC_FP16_DEV).params):
+        sim = pk.Simulation(prm)
+        sim.init_fields(np.full((40, 48), 0.5))
+        with pytest.raises(pk.LbmError) as ei:
+            sim.adjoint_seed(dj)
+        assert ei.value.code == pk.LBM_EUNSUPPORTED
+    case = W.noisy_drop(48, 40, precision=W.PREC_FP64)
+    sim = pk.Simulation(case.params)
+    sim.init_fields(case.phi, case.ux, case.uy)
+    s0 = sim.snapshot(sim.new_state_buffer())
+    with pytest.raises(pk.LbmError) as ei:
+        sim.adjoint_step(s0)
+    assert ei.value.code == pk.LBM_EINVAL
+    sim.adjoint_seed(dj)
+    with pytest.raises(pk.LbmError) as ei:
+        sim.adjoint_init(s0)
+    assert ei.value.code == pk.LBM_EUNSUPPORTED
