@@ -173,15 +173,36 @@ def cpu_baseline(case, seconds, side=512):
     o = oracle.Oracle(sub)
     o.init_fields(phi)
     o.step(1)
-    steps, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < seconds:
-        o.step(2)
-        steps += 2
-    dt = time.perf_counter() - t0
-    return {"value": side * side * steps / dt / 1e6, "unit": UNIT, "cores": oracle.get_threads(),
+
+    def timed(limit):
+        steps, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < limit:
+            o.step(2)
+            steps += 2
+        return steps, time.perf_counter() - t0
+
+    steps, dt = timed(seconds)
+    cores = oracle.get_threads()
+    oracle.set_threads(1)  # the same oracle on one core, for a fifth of the time
+    s1, d1 = timed(seconds / 5)
+    oracle.set_threads(cores)
+    return {"value": side * side * steps / dt / 1e6, "unit": UNIT, "cores": cores,
             "kind": "oracle",
             "sample": f"{side}x{side} window of the {n}x{n} initial field at the interface, "
-                      f"{steps} FP64 steps ({dt:.1f} s)"}
+                      f"{steps} FP64 steps ({dt:.1f} s)",
+            "single_core_value": side * side * s1 / d1 / 1e6, "cpu_model": cpu_model()}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name as lscpu reports it (empty if unavailable)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return ""
 
 
 def run_reference(args):
@@ -375,6 +396,32 @@ def main():
     sim.close()
     del sim
 
+    # ---- the wetting-boundary path: droplet spreading at 2048 x 1024 (walls
+    # with contact angles 30, 60, 120 degrees on the bottom, x periodic), FP32
+    wetting = None
+    if args.precision == "fp32" and not args.no_storage_compare:
+        wetting = {}
+        for th in (30.0, 60.0, 120.0):
+            sp = W.droplet_spreading(theta=th, precision=W.PREC_FP32)
+            ssim = pk.Simulation(sp.params, stream=stream)
+            ssim.init_fields(sp.phi)
+            ssim.step(args.warmup)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            nst = 10 * args.steps
+            e0.record(stream)
+            ssim.step(nst)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            wms = max_over_ranks(e0.elapsed_time(e1))
+            nodes = sp.params.nx * sp.params.ny
+            wetting[f"droplet_spreading_2048x1024_theta{int(th)}"] = {
+                "value": whole_job_mlups(world, nodes, nst, wms / 1e3), "unit": UNIT, "steps": nst,
+                "frac": bytes_per_lu * nodes * nst / (wms / 1e3) / 1e9 / peak,
+                "l2": f"state {ssim.device_bytes / 1e9:.2f} GB > L2"}
+            ssim.close()
+
     # ---- the same workload with 16-bit deviation storage (FP32 arithmetic)
     storage = None
     if args.precision == "fp32" and not args.no_storage_compare:
@@ -407,6 +454,7 @@ def main():
                            "l2": f"inputs larger than L2 (device state {state_gb:.1f} GB)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps, "clocks": clk, "storage_variants": storage,
+                "wetting_workloads": wetting,
                 "adjoint": adjoint}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -89,6 +89,7 @@ struct Phys {
   // scale s of the stored deviations and 1/s, and for f the factor
   // 1 / (1 + sum_i r_i) that makes a node's decoded populations sum to phi.
   T dv_r[2][2], dv_s[2], dv_is[2], dv_c0;
+  int seg_rows;  // rows per block segment of the TMA step (set by its launcher)
 };
 
 // Population sets are addressed in bytes through a storage codec: plane 0
@@ -1019,9 +1020,9 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
 
   const int tid = threadIdx.x;
   const int nx = P.nx, ny = P.ny;
-  const int x0 = blockIdx.x * TBX, y0 = blockIdx.y * LY;
+  const int x0 = blockIdx.x * TBX, y0 = blockIdx.y * P.seg_rows;
   const int w = min(TBX, nx - x0);
-  const int y1 = min(y0 + LY, ny);
+  const int y1 = min(y0 + P.seg_rows, ny);
   const bool active = tid < w;
   const int x = x0 + tid;
   const bool wx = P.wall_x != 0, wy = P.wall_y != 0;

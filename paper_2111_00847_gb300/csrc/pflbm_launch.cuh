@@ -26,8 +26,28 @@ cudaError_t launch_march(int model, int mode, const Phys<typename C::value_t>& P
                            : launch_march_model<C, MODEL_AC>(mode, P, B, s);
 }
 
+// Rows per block segment of the TMA step: LY, halved (down to 8) until the
+// grid holds at least two waves of resident blocks, so that grids of a few
+// million nodes still fill every SM.  Each segment re-forms two phi rows and
+// re-stages its first rows, so long segments are kept wherever the grid is
+// large enough.
+template <class C>
+static int tma_segment_rows(int nx, int ny) {
+  using G = TmaCfg<C>;
+  static int sms[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (!sms[dev] && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms[dev] = 152;
+  const long long target = 2LL * sms[dev] * (G::threads / G::TBX);
+  const long long strips = (nx + G::TBX - 1) / G::TBX;
+  int seg = LY;
+  while (seg > 8 && strips * ((ny + seg - 1) / seg) < target) seg /= 2;
+  return seg;
+}
+
 template <class C, bool UR>
-static cudaError_t launch_tma_variant(const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B,
+static cudaError_t launch_tma_variant(const Phys<typename C::value_t>& P0, const Bufs<typename C::value_t>& B,
                                       int* err, cudaStream_t s) {
   using G = TmaCfg<C>;
   using L = TmaLayout<C, G::TBX, G::DF, G::DG, G::slim>;
@@ -35,7 +55,9 @@ static cudaError_t launch_tma_variant(const Phys<typename C::value_t>& P, const 
   cudaError_t e = cudaFuncSetAttribute(k_step_tma<C, UR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L::bytes);
   if (e != cudaSuccess) return e;
-  const dim3 grid((P.nx + G::TBX - 1) / G::TBX, (P.ny + LY - 1) / LY);
+  Phys<typename C::value_t> P = P0;
+  P.seg_rows = tma_segment_rows<C>(P.nx, P.ny);
+  const dim3 grid((P.nx + G::TBX - 1) / G::TBX, (P.ny + P.seg_rows - 1) / P.seg_rows);
   k_step_tma<C, UR><<<grid, G::TBX, L::bytes, s>>>(P, B, err);
   return cudaGetLastError();
 }
