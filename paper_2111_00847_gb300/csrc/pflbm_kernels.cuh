@@ -89,7 +89,7 @@ struct Phys {
   // scale s of the stored deviations and 1/s, and for f the factor
   // 1 / (1 + sum_i r_i) that makes a node's decoded populations sum to phi.
   T dv_r[2][2], dv_s[2], dv_is[2], dv_c0;
-  int seg_rows;  // rows per block segment of the TMA step (set by its launcher)
+  int seg_rows;  // rows per block segment of the TMA step on small grids (set by its launcher)
 };
 
 // Population sets are addressed in bytes through a storage codec: plane 0
@@ -1001,7 +1001,8 @@ struct TmaCfg {
   static constexpr bool slim = fp32;
 };
 
-template <class C, bool UR>
+// VSEG: segments of P.seg_rows rows (small grids) instead of the constant LY.
+template <class C, bool UR, bool VSEG = false>
 __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>::TBX)
     k_step_tma(const Phys<typename C::value_t> P, const Bufs<typename C::value_t> B, int* __restrict__ err) {
   using T = typename C::value_t;
@@ -1020,9 +1021,10 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
 
   const int tid = threadIdx.x;
   const int nx = P.nx, ny = P.ny;
-  const int x0 = blockIdx.x * TBX, y0 = blockIdx.y * P.seg_rows;
+  const int seg = VSEG ? P.seg_rows : LY;
+  const int x0 = blockIdx.x * TBX, y0 = blockIdx.y * seg;
   const int w = min(TBX, nx - x0);
-  const int y1 = min(y0 + P.seg_rows, ny);
+  const int y1 = min(y0 + seg, ny);
   const bool active = tid < w;
   const int x = x0 + tid;
   const bool wx = P.wall_x != 0, wy = P.wall_y != 0;

@@ -46,20 +46,28 @@ static int tma_segment_rows(int nx, int ny) {
   return seg;
 }
 
-template <class C, bool UR>
-static cudaError_t launch_tma_variant(const Phys<typename C::value_t>& P0, const Bufs<typename C::value_t>& B,
-                                      int* err, cudaStream_t s) {
+template <class C, bool UR, bool VSEG>
+static cudaError_t launch_tma_seg(const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B,
+                                  int* err, cudaStream_t s) {
   using G = TmaCfg<C>;
   using L = TmaLayout<C, G::TBX, G::DF, G::DG, G::slim>;
   // per function and device; cheap next to a step
-  cudaError_t e = cudaFuncSetAttribute(k_step_tma<C, UR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_step_tma<C, UR, VSEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L::bytes);
   if (e != cudaSuccess) return e;
+  const dim3 grid((P.nx + G::TBX - 1) / G::TBX, (P.ny + P.seg_rows - 1) / P.seg_rows);
+  k_step_tma<C, UR, VSEG><<<grid, G::TBX, L::bytes, s>>>(P, B, err);
+  return cudaGetLastError();
+}
+
+// Segments of LY rows use the instantiation with the constant length (its
+// register allocation is the tuned one); shorter ones the runtime-length one.
+template <class C, bool UR>
+static cudaError_t launch_tma_variant(const Phys<typename C::value_t>& P0, const Bufs<typename C::value_t>& B,
+                                      int* err, cudaStream_t s) {
   Phys<typename C::value_t> P = P0;
   P.seg_rows = tma_segment_rows<C>(P.nx, P.ny);
-  const dim3 grid((P.nx + G::TBX - 1) / G::TBX, (P.ny + P.seg_rows - 1) / P.seg_rows);
-  k_step_tma<C, UR><<<grid, G::TBX, L::bytes, s>>>(P, B, err);
-  return cudaGetLastError();
+  return P.seg_rows == LY ? launch_tma_seg<C, UR, false>(P, B, err, s) : launch_tma_seg<C, UR, true>(P, B, err, s);
 }
 
 // The launch shape per storage codec (strip width, staging depth, blocks
