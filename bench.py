@@ -339,12 +339,12 @@ def main():
     stream = torch.cuda.current_stream(dev)
     peak, peak_src = measured_peak()
 
-    def timed_steps(params, label, per_lu_bytes):
+    def timed_steps(params, label, per_lu_bytes, phi0=None):
         """W warm-up steps, then K steps timed with CUDA events on the
         simulation's stream (barrier + synchronize on both sides); the
         roofline of the fused step kernel (one launch per step)."""
         s = pk.Simulation(params, stream=stream)
-        s.init_fields(case.phi)
+        s.init_fields(case.phi if phi0 is None else phi0)
         s.step(args.warmup)
         torch.cuda.synchronize()
         clk_s = ClockSampler(local)
@@ -422,6 +422,16 @@ def main():
                 "l2": f"state {ssim.device_bytes / 1e9:.2f} GB > L2"}
             ssim.close()
 
+    # ---- the Cahn-Hilliard alternative on the same workload (phi in [-1, 1])
+    models = None
+    if args.precision == "fp32" and not args.no_storage_compare:
+        chp = case.params.with_(phase_model=W.MODEL_CH, phiA=1.0, phiB=-1.0)
+        sch, msch, roofch, clkch = timed_steps(chp, "fp32_ch", bytes_per_lu, 2.0 * case.phi - 1.0)
+        sch.close()
+        del sch
+        models = {"cahn_hilliard": {"value": whole_job_mlups(world, N, args.steps, msch / 1e3), "unit": UNIT,
+                                    "ms_per_step": msch / args.steps, "roofline": roofch, "clocks": clkch}}
+
     # ---- the same workload with 16-bit deviation storage (FP32 arithmetic)
     storage = None
     if args.precision == "fp32" and not args.no_storage_compare:
@@ -454,7 +464,7 @@ def main():
                            "l2": f"inputs larger than L2 (device state {state_gb:.1f} GB)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps, "clocks": clk, "storage_variants": storage,
-                "wetting_workloads": wetting,
+                "wetting_workloads": wetting, "model_variants": models,
                 "adjoint": adjoint}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -333,6 +333,8 @@ static int do_step(lbm_handle* h, int64_t n) {
     cudaError_t e = cudaErrorNotSupported;
     if (h->use_tma && h->prm.phase_model == LBM_AC)
       e = launch_step_tma<C>(P, B, h->derr, h->unit_rates, h->stream);
+    else if (h->use_tma && h->prm.phase_model == LBM_CH)
+      e = launch_step_tma_ch<C>(P, B, h->derr, h->unit_rates, h->stream);
     if (e == cudaErrorNotSupported) e = launch_march<C>(h->prm.phase_model, MODE_STEP, P, B, h->stream);
     CUDA_TRY(h, e);
     h->cur ^= 1;

@@ -1277,6 +1277,339 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
 }
 
 // ---------------------------------------------------------------------------
+// TMA-staged fused step, Cahn-Hilliard phase field (D = grad mu_phi, Eq. (6)).
+//
+// The same staging as k_step_tma, with the wider reach of the CH update: the
+// node update of row y reads mu_phi on rows y-1 .. y+1, and mu_phi of a row
+// needs the Laplacian of phi (Eq. (5)), so phi runs two rows and two columns
+// ahead.  Per march step y: phi of row y+2 from the staged f rows y+1 .. y+3
+// (a ghost row above a top wall); barrier; mu_phi of row y+1 over columns
+// -1 .. w from phi rows y .. y+2 (mirrored at walls, as the oracle's ghost
+// rule for mu); barrier; the node update of row y.  Segment starts form phi
+// of rows y0-2 and y0-1 from pulls of the global planes, and phi of y0, y0+1
+// and mu_phi of y0-1, y0 from the staged rows.
+// ---------------------------------------------------------------------------
+template <class C>
+struct TmaChCfg {
+  static constexpr int TBX = 128;
+  static constexpr int DF = 1, DG = 1;
+  static constexpr int threads = sizeof(typename C::value_t) == 8 ? 256 : 512;
+};
+constexpr int CH_PRING = 8;  // phi rows (power of two): rows y-2 .. y+2 may be in use
+constexpr int CH_MRING = 4;  // mu_phi rows (power of two): rows y-2 .. y+1
+
+template <class C, int TBX, int DF, int DG>
+struct TmaChLayout {
+  using T = typename C::value_t;
+  static constexpr int SEG = Seg<TBX>::value;
+  static constexpr int RF = 5 + DF, RG = 3 + DG;  // f rows y-1 .. y+3 live, g rows y-1 .. y+1
+  static constexpr int PW = TBX + 4, MW = TBX + 2;  // phi columns -2 .. w+1, mu columns -1 .. w
+  static constexpr size_t P0 = (size_t)SEG * C::B0;
+  static constexpr size_t PI = (size_t)SEG * C::BI;
+  static constexpr size_t SLOT = P0 + 8 * PI;
+  static constexpr size_t f_off = 0;
+  static constexpr size_t g_off = f_off + RF * SLOT;
+  static constexpr size_t phi_off = g_off + RG * SLOT;
+  static constexpr size_t mu_off = phi_off + sizeof(T) * CH_PRING * PW;
+  static constexpr size_t bar_off = mu_off + sizeof(T) * CH_MRING * MW;
+  static constexpr size_t bytes = bar_off + 8 * (RF + RG);
+  static_assert(g_off % 16 == 0 && phi_off % 16 == 0 && mu_off % 16 == 0 && bar_off % 8 == 0,
+                "smem layout alignment");
+  static_assert(P0 % 16 == 0 && PI % 16 == 0, "bulk-copy segments must be 16-byte multiples");
+};
+
+template <class C, bool UR, bool VSEG = false>
+__global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaChCfg<C>::TBX)
+    k_step_tma_ch(const Phys<typename C::value_t> P, const Bufs<typename C::value_t> B, int* __restrict__ err) {
+  using T = typename C::value_t;
+  constexpr int TBX = TmaChCfg<C>::TBX, DF = TmaChCfg<C>::DF, DG = TmaChCfg<C>::DG;
+  using L = TmaChLayout<C, TBX, DF, DG>;
+  constexpr int SEG = L::SEG, RF = L::RF, RG = L::RG, PW = L::PW, MW = L::MW;
+  constexpr int FS = (int)L::SLOT;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* const sf = smem + L::f_off;
+  unsigned char* const sg = smem + L::g_off;
+  T* const sp = reinterpret_cast<T*>(smem + L::phi_off);  // [CH_PRING][PW], column c at c + 2
+  T* const sm = reinterpret_cast<T*>(smem + L::mu_off);   // [CH_MRING][MW], column c at c + 1
+  uint64_t* const barF = reinterpret_cast<uint64_t*>(smem + L::bar_off);
+  uint64_t* const barG = barF + RF;
+
+  const int tid = threadIdx.x;
+  const int nx = P.nx, ny = P.ny;
+  const int seg = VSEG ? P.seg_rows : LY;
+  const int x0 = blockIdx.x * TBX, y0 = blockIdx.y * seg;
+  const int w = min(TBX, nx - x0);
+  const int y1 = min(y0 + seg, ny);
+  const bool active = tid < w;
+  const int x = x0 + tid;
+  const bool wx = P.wall_x != 0, wy = P.wall_y != 0;
+  const int fbase = y0 - 1, gbase = y0 - 1;  // first staged f / g row
+  const uint32_t seg0 = (uint32_t)((((w + 2 * XPAD) * C::B0 + 15) / 16) * 16);
+  const uint32_t segI = (uint32_t)((((w + 2 * XPAD) * C::BI + 15) / 16) * 16);
+  const long long RB = pop_row_bytes<C>(P.pitch);
+  const T rf2[2] = {P.dv_r[0][0], P.dv_r[0][1]}, rg2[2] = {P.dv_r[1][0], P.dv_r[1][1]};
+  const T isf = P.dv_is[0], isg = P.dv_is[1];
+  const int f_last = y1 + 2, g_last = y1;  // last f / g row any output row needs
+  const bool edge_x = wx && (x0 == 0 || x0 + w == nx);
+
+  if (tid == 0) {
+    for (int k = 0; k < RF + RG; ++k) mbar_init(&barF[k], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  auto wrap_row = [&](int r) { return r < 0 ? r + ny : (r >= ny ? r - ny : r); };
+  auto stage = [&](const void* src, unsigned char* slot, uint64_t* bar, int r) {
+    if ((r < 0 || r >= ny) && wy) {
+      mbar_arrive(bar);
+      return;
+    }
+    const unsigned char* row = static_cast<const unsigned char*>(src) + (long long)wrap_row(r) * RB;
+    mbar_arrive_expect_tx(bar, seg0 + 8u * segI);
+    bulk_g2s(slot, row + (long long)x0 * C::B0, seg0, bar);
+#pragma unroll 1
+    for (int i = 1; i < 9; ++i)
+      bulk_g2s(slot + L::P0 + (i - 1) * L::PI, row + pop_plane_off<C>(P.pitch, i) + (long long)x0 * C::BI,
+               segI, bar);
+  };
+  auto fidx = [&](int r) { return (r - fbase) % RF; };
+  auto gidx = [&](int r) { return (r - gbase) % RG; };
+  auto fslot = [&](int r) { return sf + fidx(r) * FS; };
+  auto gslot = [&](int r) { return sg + gidx(r) * FS; };
+  auto wait_f = [&](int r) { return mbar_wait_bounded(&barF[fidx(r)], ((r - fbase) / RF) & 1); };
+  auto wait_g = [&](int r) { return mbar_wait_bounded(&barG[gidx(r)], ((r - gbase) / RG) & 1); };
+  auto prow = [&](int r) { return sp + (r & (CH_PRING - 1)) * PW; };
+  auto mrow = [&](int r) { return sm + (r & (CH_MRING - 1)) * MW; };
+
+  // phi of row r (in the domain or wrapped) from the staged slots: own column,
+  // thread 0 columns -1 and -2, thread w-1 columns w and w+1; at an x wall the
+  // ghost column from the wetting rule (the column beyond it is not needed:
+  // mu_phi is mirrored there).
+  auto phi_row_at = [&](int r, const unsigned char* rm, const unsigned char* r0, const unsigned char* rp) {
+    const int rr = wrap_row(r);
+    const bool bym = wy && rr == 0, byp = wy && rr == ny - 1;
+    T* dst = prow(r);
+    if (!active) return;
+    T v[9];
+    if (edge_x || bym || byp)
+      pull_staged<C, SEG>(rm, r0, rp, tid + XPAD, wx && x == 0, wx && x == nx - 1, bym, byp, rf2, isf, v);
+    else
+      pull_staged<C, SEG>(rm, r0, rp, tid + XPAD, false, false, false, false, rf2, isf, v);
+    const T ph = sum9(v);
+    dst[tid + 2] = ph;
+    if (tid == 0) {
+      if (x0 > 0 || !wx) {
+        pull_staged<C, SEG>(rm, r0, rp, XPAD - 1, false, wx && x0 - 1 == nx - 1, bym, byp, rf2, isf, v);
+        dst[1] = sum9(v);
+        pull_staged<C, SEG>(rm, r0, rp, XPAD - 2, false, wx && x0 - 2 == nx - 1, bym, byp, rf2, isf, v);
+        dst[0] = sum9(v);
+      } else {
+        pull_staged<C, SEG>(rm, r0, rp, XPAD + 1, false, wx && 1 == nx - 1, bym, byp, rf2, isf, v);
+        dst[1] = wall_ghost(P, SIDE_LEFT, ph, sum9(v));
+        dst[0] = T(0);
+      }
+    }
+    if (tid == w - 1) {
+      if (x0 + w < nx || !wx) {
+        pull_staged<C, SEG>(rm, r0, rp, XPAD + w, wx && x0 + w == 0, wx && x0 + w == nx - 1, bym, byp, rf2, isf,
+                            v);
+        const T pw = sum9(v);
+        dst[w + 2] = pw;
+        if (wx && x0 + w + 1 == nx) {  // column w is the last node: w+1 is the wall ghost
+          dst[w + 3] = wall_ghost(P, SIDE_RIGHT, pw, ph);
+        } else {
+          pull_staged<C, SEG>(rm, r0, rp, XPAD + w + 1, false, wx && x0 + w + 1 == nx - 1, bym, byp, rf2, isf, v);
+          dst[w + 3] = sum9(v);
+        }
+      } else {
+        pull_staged<C, SEG>(rm, r0, rp, XPAD + w - 2, wx && nx - 2 == 0, false, bym, byp, rf2, isf, v);
+        dst[w + 2] = wall_ghost(P, SIDE_RIGHT, ph, sum9(v));
+        dst[w + 3] = T(0);
+      }
+    }
+  };
+  // the same from pulls of the global planes (segment starts)
+  auto phi_row_global = [&](int r) {
+    const int rr = wrap_row(r);
+    T* dst = prow(r);
+    if (!active) return;
+    const T ph = phi_at<C, MODE_STEP>(P, B, x, rr);
+    dst[tid + 2] = ph;
+    if (tid == 0) {
+      if (x0 > 0 || !wx) {
+        const int a = x0 > 0 ? x0 - 1 : nx - 1, b = x0 > 1 ? x0 - 2 : x0 - 2 + nx;
+        dst[1] = phi_at<C, MODE_STEP>(P, B, a, rr);
+        dst[0] = phi_at<C, MODE_STEP>(P, B, b, rr);
+      } else {
+        dst[1] = wall_ghost(P, SIDE_LEFT, ph, phi_at<C, MODE_STEP>(P, B, 1, rr));
+        dst[0] = T(0);
+      }
+    }
+    if (tid == w - 1) {
+      if (x0 + w < nx || !wx) {
+        const int a = x0 + w < nx ? x0 + w : x0 + w - nx;
+        const int b = x0 + w + 1 < nx ? x0 + w + 1 : x0 + w + 1 - nx;
+        const T pw = phi_at<C, MODE_STEP>(P, B, a, rr);
+        dst[w + 2] = pw;
+        dst[w + 3] = (wx && x0 + w + 1 == nx) ? wall_ghost(P, SIDE_RIGHT, pw, ph) : phi_at<C, MODE_STEP>(P, B, b, rr);
+      } else {
+        dst[w + 2] = wall_ghost(P, SIDE_RIGHT, ph, phi_at<C, MODE_STEP>(P, B, nx - 2, rr));
+        dst[w + 3] = T(0);
+      }
+    }
+  };
+  // ghost phi row beyond a y wall over every ring column, from rows r1, r2
+  auto ghost_row = [&](int rg, int r1, int r2, int side) {
+    T* d = prow(rg);
+    const T* a = prow(r1);
+    const T* b = prow(r2);
+    for (int j = tid; j < w + 4; j += TBX) d[j] = wall_ghost(P, side, a[j], b[j]);
+  };
+  // mu_phi (Eq. (5)) at ring column j of a row, from phi rows r-1, r, r+1
+  auto mu_at = [&](const T* pm, const T* p0, const T* pp, int j) {
+    const T ph = p0[j];
+    const T lap = (((p0[j + 1] - ph) + (p0[j - 1] - ph)) + ((pp[j] - ph) + (pm[j] - ph))) * T(2.0 / 3.0) +
+                  (((pp[j + 1] - ph) + (pm[j - 1] - ph)) + ((pp[j - 1] - ph) + (pm[j + 1] - ph))) * T(1.0 / 6.0);
+    return P.beta4 * (ph - P.phiA) * (ph - P.phiB) * (ph - P.phibar) - P.kappa * lap;
+  };
+  // mu_phi of row r over columns -1 .. w; at an x wall the halo column
+  // mirrors the column next to the wall (written by the thread owning it)
+  auto mu_row = [&](int r) {
+    const T* pm = prow(r - 1);
+    const T* p0 = prow(r);
+    const T* pp = prow(r + 1);
+    T* d = mrow(r);
+    if (!active) return;
+    const T mo = mu_at(pm, p0, pp, tid + 2);
+    d[tid + 1] = mo;
+    if (tid == 0) d[0] = (wx && x0 == 0) ? mo : mu_at(pm, p0, pp, 1);
+    if (tid == w - 1) d[w + 1] = (wx && x0 + w == nx) ? mo : mu_at(pm, p0, pp, w + 2);
+  };
+  // mirrored mu_phi row beyond a y wall
+  auto mu_copy_row = [&](int rdst, int rsrc) {
+    T* d = mrow(rdst);
+    const T* s = mrow(rsrc);
+    for (int j = tid; j < w + 2; j += TBX) d[j] = s[j];
+  };
+
+  bool ok = true;
+  // ---------------------------------------------------------------- prologue
+  if (tid == 0) {
+    for (int r = fbase; r <= min(y0 + 2 + DF, f_last); ++r) stage(B.fin, fslot(r), &barF[fidx(r)], r);
+    for (int r = gbase; r <= min(y0 + DG, g_last); ++r) stage(B.gin, gslot(r), &barG[gidx(r)], r);
+  }
+  for (int r = fbase; r <= min(y0 + 2, f_last); ++r) ok = wait_f(r) && ok;
+  for (int r = gbase; r <= min(y0, g_last); ++r) ok = wait_g(r) && ok;
+  for (int r = y0 - 2; r <= y0 - 1; ++r)
+    if ((r >= 0 && r < ny) || !wy) phi_row_global(r);
+  for (int r = y0; r <= y0 + 1; ++r)
+    if (r < ny || !wy) phi_row_at(r, fslot(r - 1), fslot(r), fslot(r + 1));
+  bool failed = __syncthreads_or(!ok);
+  if (!failed && wy && (y0 <= 1 || y0 + 1 == ny)) {
+    if (y0 <= 1) ghost_row(-1, 0, 1, SIDE_BOTTOM);
+    if (y0 + 1 == ny) ghost_row(ny, ny - 1, ny - 2, SIDE_TOP);
+    __syncthreads();
+  }
+  if (!failed) {
+    for (int r = y0 - 1; r <= y0; ++r)
+      if ((r >= 0 && r < ny) || !wy) mu_row(r);
+    __syncthreads();
+    if (wy && y0 == 0) {
+      mu_copy_row(-1, 0);
+      __syncthreads();
+    }
+  }
+  T h[5] = {T(0), T(0), T(0), T(0), T(0)};
+  if (active) {
+    const T* hb = B.hist + ix(P, 5, 0, x, y0);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) h[k] = hb[k * P.pitch];
+  }
+
+  // ---------------------------------------------------------------- march
+  for (int y = y0; y < y1 && !failed; ++y) {
+    ok = true;
+    if (y + 3 <= f_last) ok = wait_f(y + 3) && ok;
+    if (y + 1 <= g_last) ok = wait_g(y + 1) && ok;
+    const int r2 = y + 2;
+    if (r2 < ny || !wy) phi_row_at(r2, fslot(r2 - 1), fslot(r2), fslot(r2 + 1));
+    else if (r2 == ny) ghost_row(ny, ny - 1, ny - 2, SIDE_TOP);  // rows ny-1, ny-2 complete
+    failed = __syncthreads_or(!ok);
+    if (failed) break;
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      const int rf = y + 3 + DF, rg = y + 1 + DG;  // into the slots of rows y-2
+      if (rf <= f_last) stage(B.fin, fslot(rf), &barF[fidx(rf)], rf);
+      if (rg <= g_last) stage(B.gin, gslot(rg), &barG[gidx(rg)], rg);
+    }
+    const int r1 = y + 1;
+    if (r1 < ny || !wy) mu_row(r1);
+    else if (r1 == ny) mu_copy_row(ny, ny - 1);
+    __syncthreads();
+    T hn[5] = {T(0), T(0), T(0), T(0), T(0)};
+    if (active && y + 1 < y1) {
+      const T* hb = B.hist + ix(P, 5, 0, x, y + 1);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) hn[k] = hb[k * P.pitch];
+    }
+    if (active) {
+      const T* pm = prow(y - 1);
+      const T* p0 = prow(y);
+      const T* pp = prow(y + 1);
+      const int c = tid + 2;
+      T phi9[9];
+      phi9[0] = p0[c];
+      phi9[1] = p0[c + 1];
+      phi9[2] = pp[c];
+      phi9[3] = p0[c - 1];
+      phi9[4] = pm[c];
+      phi9[5] = pp[c + 1];
+      phi9[6] = pp[c - 1];
+      phi9[7] = pm[c - 1];
+      phi9[8] = pm[c + 1];
+      const T* mm = mrow(y - 1);
+      const T* m0 = mrow(y);
+      const T* mp = mrow(y + 1);
+      const int cm = tid + 1;
+      T mu9[9];
+      mu9[0] = m0[cm];
+      mu9[1] = m0[cm + 1];
+      mu9[2] = mp[cm];
+      mu9[3] = m0[cm - 1];
+      mu9[4] = mm[cm];
+      mu9[5] = mp[cm + 1];
+      mu9[6] = mp[cm - 1];
+      mu9[7] = mm[cm - 1];
+      mu9[8] = mm[cm + 1];
+      const bool bym = wy && y == 0, byp = wy && y == ny - 1;
+      T f[9], g[9];
+      if (edge_x || bym || byp) {
+        const bool bxm = wx && x == 0, bxp = wx && x == nx - 1;
+        pull_staged<C, SEG>(fslot(y - 1), fslot(y), fslot(y + 1), tid + XPAD, bxm, bxp, bym, byp, rf2, isf, f);
+        pull_staged<C, SEG>(gslot(y - 1), gslot(y), gslot(y + 1), tid + XPAD, bxm, bxp, bym, byp, rg2, isg, g);
+      } else {
+        pull_staged<C, SEG>(fslot(y - 1), fslot(y), fslot(y + 1), tid + XPAD, false, false, false, false, rf2,
+                            isf, f);
+        pull_staged<C, SEG>(gslot(y - 1), gslot(y), gslot(y + 1), tid + XPAD, false, false, false, false, rg2,
+                            isg, g);
+      }
+      node_update<C, MODEL_CH, MODE_STEP, UR>(P, B, x, y, phi9, mu9, f, g, h, T(0), T(0), T(0));
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) h[k] = hn[k];
+  }
+  if (failed) {
+    if (tid == 0) {
+      atomicOr(err, 1);
+      for (int k = 0; k < RF + RG; ++k) {
+        for (int q = 0; q < 2; ++q) mbar_wait_bounded(&barF[k], q, MBAR_DRAIN_LIMIT);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Auxiliary kernels: gather the pulled populations, scatter populations back
 // into the pre-stream layout, convert planes, diagnostics reductions.
 // ---------------------------------------------------------------------------

@@ -70,6 +70,43 @@ static cudaError_t launch_tma_variant(const Phys<typename C::value_t>& P0, const
   return P.seg_rows == LY ? launch_tma_seg<C, UR, false>(P, B, err, s) : launch_tma_seg<C, UR, true>(P, B, err, s);
 }
 
+// Cahn-Hilliard step: same segment rule, its own launch shape (TmaChCfg).
+template <class C>
+static int tma_ch_segment_rows(int nx, int ny) {
+  using G = TmaChCfg<C>;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long target = 2LL * sms * (G::threads / G::TBX);
+  const long long strips = (nx + G::TBX - 1) / G::TBX;
+  int seg = LY;
+  while (seg > 8 && strips * ((ny + seg - 1) / seg) < target) seg /= 2;
+  return seg;
+}
+
+template <class C, bool UR, bool VSEG>
+static cudaError_t launch_tma_ch_seg(const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B,
+                                     int* err, cudaStream_t s) {
+  using G = TmaChCfg<C>;
+  using L = TmaChLayout<C, G::TBX, G::DF, G::DG>;
+  cudaError_t e = cudaFuncSetAttribute(k_step_tma_ch<C, UR, VSEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)L::bytes);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((P.nx + G::TBX - 1) / G::TBX, (P.ny + P.seg_rows - 1) / P.seg_rows);
+  k_step_tma_ch<C, UR, VSEG><<<grid, G::TBX, L::bytes, s>>>(P, B, err);
+  return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_step_tma_ch(const Phys<typename C::value_t>& P0, const Bufs<typename C::value_t>& B, int* err,
+                               bool unit_rates, cudaStream_t s) {
+  if (P0.nx < 4 * XPAD) return cudaErrorNotSupported;
+  Phys<typename C::value_t> P = P0;
+  P.seg_rows = tma_ch_segment_rows<C>(P.nx, P.ny);
+  if (P.seg_rows == LY)
+    return unit_rates ? launch_tma_ch_seg<C, true, false>(P, B, err, s) : launch_tma_ch_seg<C, false, false>(P, B, err, s);
+  return unit_rates ? launch_tma_ch_seg<C, true, true>(P, B, err, s) : launch_tma_ch_seg<C, false, true>(P, B, err, s);
+}
+
 // The launch shape per storage codec (strip width, staging depth, blocks
 // per SM) and the measurements behind it are given with TmaCfg.
 template <class C>
@@ -178,7 +215,9 @@ cudaError_t launch_adjoint_init(const Phys<T>& P, const AdjBufs& A, double* out,
   template cudaError_t launch_march<C>(int, int, const Phys<C::value_t>&, const Bufs<C::value_t>&,  \
                                        cudaStream_t);                                               \
   template cudaError_t launch_step_tma<C>(const Phys<C::value_t>&, const Bufs<C::value_t>&, int*,   \
-                                          bool, cudaStream_t);
+                                          bool, cudaStream_t);                                      \
+  template cudaError_t launch_step_tma_ch<C>(const Phys<C::value_t>&, const Bufs<C::value_t>&, int*, \
+                                             bool, cudaStream_t);
 
 #define PFLBM_INSTANTIATE_DEV(C)                                                                    \
   PFLBM_INSTANTIATE_CODEC(C)                                                                        \

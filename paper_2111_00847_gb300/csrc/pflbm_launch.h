@@ -21,6 +21,10 @@ cudaError_t launch_march(int model, int mode, const Phys<typename C::value_t>& P
 template <class C>
 cudaError_t launch_step_tma(const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B, int* err,
                             bool unit_rates, cudaStream_t s);
+// TMA-staged Cahn-Hilliard step (the same contract)
+template <class C>
+cudaError_t launch_step_tma_ch(const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B, int* err,
+                               bool unit_rates, cudaStream_t s);
 // deviation storage: pulled plane k of a set -> dense doubles of a region
 template <class C>
 cudaError_t launch_pull_export(const Phys<typename C::value_t>& P, const void* in, int set, int k, double* out,

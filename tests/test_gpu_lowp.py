@@ -122,15 +122,16 @@ def test_lowp_total_phi_drift(pk, prec, walls):
     assert abs(s1 - s0) <= 1e-5 * abs(s0)
 
 
+@pytest.mark.parametrize("model", [W.MODEL_AC, W.MODEL_CH], ids=["ac", "ch"])
 @pytest.mark.parametrize("prec", LOWP, ids=LOWP_IDS)
 @pytest.mark.parametrize("walls", ["none", "y", "x", "all"])
 @pytest.mark.parametrize("nx,ny", [(300, 150), (16, 70), (257, 129)])
-def test_lowp_tma_kernel_matches_register_kernel(pk, prec, walls, nx, ny):
+def test_lowp_tma_kernel_matches_register_kernel(pk, prec, walls, nx, ny, model):
     """Both step kernels decode, update and encode the same way; they differ
     only in FP32 rounding (operation order), which can move a deviation to
     the neighbouring 16-bit value.  After one step they agree to a fraction
     of u, after 20 steps to the parity bar."""
-    case = W.noisy_drop(nx, ny, precision=prec, walls=walls, noise=0.005, u_amp=0.002,
+    case = W.noisy_drop(nx, ny, precision=prec, walls=walls, noise=0.005, u_amp=0.002, model=model,
                         theta=(60, 120, 45, 135), gravity=(W.GRAV_RHO, 1e-6, -1e-5))
     u = U16[prec]
     sims = []

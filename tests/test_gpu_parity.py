@@ -326,15 +326,18 @@ def test_full_size_sampled_windows(pk, oracle_mod, n):
         assert dg <= 1e-5 * gmax, (y0, dg / gmax)
 
 
+@pytest.mark.parametrize("model", [W.MODEL_AC, W.MODEL_CH], ids=["ac", "ch"])
 @pytest.mark.parametrize("prec", [W.PREC_FP64, W.PREC_FP32])
 @pytest.mark.parametrize("walls", ["none", "y", "x", "all"])
-@pytest.mark.parametrize("nx,ny", [(300, 150), (16, 70), (257, 129)])
-def test_tma_kernel_matches_register_kernel(pk, prec, walls, nx, ny):
-    """The TMA-staged step and the register-pipelined step compute the same
-    update from the same pulled values (the TMA kernel relaxes the unit-rate
-    moments as m^eq + m_src/2 instead of m + (m^eq - m) + m_src/2).  After one
-    step they agree to rounding, after 20 steps to the parity bar."""
-    case = W.noisy_drop(nx, ny, precision=prec, walls=walls, noise=0.005, u_amp=0.002,
+@pytest.mark.parametrize("nx,ny", [(300, 150), (16, 70), (257, 129), (129, 200)])
+def test_tma_kernel_matches_register_kernel(pk, prec, walls, nx, ny, model):
+    """The TMA-staged steps (Allen-Cahn and Cahn-Hilliard) and the
+    register-pipelined step compute the same update from the same pulled
+    values (the TMA kernels relax the unit-rate moments as m^eq + m_src/2
+    instead of m + (m^eq - m) + m_src/2).  After one step they agree to
+    rounding, after 20 steps to the parity bar.  129 columns leave a last
+    strip of one column; 200 rows several segments and a ragged one."""
+    case = W.noisy_drop(nx, ny, precision=prec, walls=walls, noise=0.005, u_amp=0.002, model=model,
                         theta=(60, 120, 45, 135), gravity=(W.GRAV_RHO, 1e-6, -1e-5))
     sims = []
     for flags in (0, pk.LBM_FLAG_NO_TMA):
