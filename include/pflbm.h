@@ -119,8 +119,10 @@ enum {
  *               steps (and then synchronises) and fails with LBM_EUNSTABLE
  *               on a non-finite value or |u| > 0.4
  *  flags        LBM_FLAG_NO_TMA: step with the register-pipelined kernel
- *               instead of the TMA-staged one (same arithmetic, for A/B
- *               comparison); 0 otherwise
+ *               instead of the TMA-staged ones (Allen-Cahn and
+ *               Cahn-Hilliard; same arithmetic, for A/B comparison);
+ *               0 otherwise.  Grids under 16 columns always use the
+ *               register-pipelined kernel.
  */
 typedef struct lbm_params {
     int32_t version, nx, ny, precision;

@@ -31,19 +31,30 @@ cudaError_t launch_march(int model, int mode, const Phys<typename C::value_t>& P
 // million nodes still fill every SM.  Each segment re-forms two phi rows and
 // re-stages its first rows, so long segments are kept wherever the grid is
 // large enough.
-template <class C>
-static int tma_segment_rows(int nx, int ny) {
-  using G = TmaCfg<C>;
+// Number of SMs of the current device (looked up once per device).
+static inline int device_sm_count() {
   static int sms[64] = {0};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
   if (!sms[dev] && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     sms[dev] = 152;
-  const long long target = 2LL * sms[dev] * (G::threads / G::TBX);
-  const long long strips = (nx + G::TBX - 1) / G::TBX;
+  return sms[dev];
+}
+
+// Rows per block segment: LY, halved (down to 8) until a grid of strips of
+// `tbx` columns holds at least two waves of `per_sm` resident blocks.
+static inline int segment_rows(int nx, int ny, int tbx, int per_sm) {
+  const long long target = 2LL * device_sm_count() * per_sm;
+  const long long strips = (nx + tbx - 1) / tbx;
   int seg = LY;
   while (seg > 8 && strips * ((ny + seg - 1) / seg) < target) seg /= 2;
   return seg;
+}
+
+template <class C>
+static int tma_segment_rows(int nx, int ny) {
+  using G = TmaCfg<C>;
+  return segment_rows(nx, ny, G::TBX, G::threads / G::TBX);
 }
 
 template <class C, bool UR, bool VSEG>
@@ -74,13 +85,7 @@ static cudaError_t launch_tma_variant(const Phys<typename C::value_t>& P0, const
 template <class C>
 static int tma_ch_segment_rows(int nx, int ny) {
   using G = TmaChCfg<C>;
-  int dev = 0, sms = 152;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long target = 2LL * sms * (G::threads / G::TBX);
-  const long long strips = (nx + G::TBX - 1) / G::TBX;
-  int seg = LY;
-  while (seg > 8 && strips * ((ny + seg - 1) / seg) < target) seg /= 2;
-  return seg;
+  return segment_rows(nx, ny, G::TBX, G::threads / G::TBX);
 }
 
 template <class C, bool UR, bool VSEG>
