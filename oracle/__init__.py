@@ -84,6 +84,8 @@ def lib():
         L.oracle_step.argtypes = [C.c_void_p, C.c_int64]
         L.oracle_fields.argtypes = [C.c_void_p, C.c_int32, dp]
         L.oracle_set_fields.argtypes = [C.c_void_p, C.c_int32, dp]
+        L.oracle_set_solid.argtypes = [C.c_void_p, C.POINTER(C.c_uint8)]
+        L.oracle_padded.argtypes = [C.c_void_p, C.c_int32, dp]
         L.oracle_destroy.argtypes = [C.c_void_p]
         L.oracle_destroy.restype = None
         L.oracle_last_error.argtypes = [C.c_void_p]
@@ -158,6 +160,17 @@ class Oracle:
         assert a.shape == (self.ny, self.nx), a.shape
         return a
 
+    def set_solid(self, mask):
+        """Solid nodes: mask [ny][nx], nonzero = solid (None removes them)."""
+        if mask is None:
+            self._solid = None
+            self._check(lib().oracle_set_solid(self._h, None))
+            return
+        m = np.ascontiguousarray(np.asarray(mask) != 0, dtype=np.uint8)
+        assert m.shape == (self.ny, self.nx), m.shape
+        self._solid = m
+        self._check(lib().oracle_set_solid(self._h, m.ctypes.data_as(C.POINTER(C.c_uint8))))
+
     def init_fields(self, phi, ux=None, uy=None, p=None):
         arrs = [self._arr(x) for x in (phi, ux, uy, p)]
         self._keep = arrs
@@ -184,6 +197,13 @@ class Oracle:
         self._check(lib().oracle_fields(self._h, int(which), _dptr(out)))
         return out
 
+    def padded(self, which: int = 0) -> np.ndarray:
+        """[ny+2][nx+2] phi (which 0) or mu_phi (1) as the last macro pass's
+        stencils saw them (ghost layer included)."""
+        out = np.empty((self.ny + 2, self.nx + 2))
+        self._check(lib().oracle_padded(self._h, int(which), _dptr(out)))
+        return out
+
     def set_fields(self, which: int, arr: np.ndarray):
         a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64))
         self._check(lib().oracle_set_fields(self._h, int(which), _dptr(a)))
@@ -195,6 +215,8 @@ class Oracle:
 
 def run_case(case, steps: int | None = None) -> Oracle:
     o = Oracle(case.params)
+    if getattr(case, "solid", None) is not None:
+        o.set_solid(case.solid)
     o.init_fields(case.phi, case.ux, case.uy, case.p)
     o.step(case.steps if steps is None else steps)
     return o

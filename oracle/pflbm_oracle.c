@@ -34,6 +34,12 @@
  *      vectors of Eqs. (C.2)-(C.4) and the relaxation rules of Sec. 4
  *  10. streaming with half-way bounce-back (Sec. 4)
  *
+ * Solid obstacles (optional, oracle_set_solid): a node marked solid takes no
+ * part in the flow.  A link whose upstream node is solid reflects like a
+ * wall link (half-way bounce-back, Sec. 4), and the stencils of step 3 see
+ * at a solid node the neutral-wetting value of the field (mean over its fluid
+ * neighbours, fill_pad).  Every per-node output at a solid node is zero.
+ *
  * Parity notes (readings of points the paper leaves open) are stated where
  * they are used: the guard on n, the stable form of the wetting root, the
  * ghost value next to a wall, the initial populations and history.
@@ -139,6 +145,7 @@ typedef struct {
     double *rho, *ux, *uy, *p, *mcx, *mcy, *Fx, *Fy, *s78;
     double *cur[5], *dt[5];
     double diag[O_NDIAG];
+    unsigned char *solid;     /* NULL, or [ny][nx] with 1 at solid nodes */
     int wet_flag;
     char err[256];
 } ostate;
@@ -204,27 +211,70 @@ static double wall_ghost(const oracle_params *P, double phi1, double phi2, doubl
 }
 
 /* ------------------------------------------------------------------ */
-/* Padded copy of a node field with one ghost layer.  x sides first,   */
-/* then y sides over the extended x range (so corners take the y rule  */
-/* applied to the x ghosts).  Periodic sides wrap; wall sides use the  */
-/* wetting ghost (wetting != 0) or the mirror value (wetting == 0).    */
+/* Padded copy of a node field with one ghost layer.  Solid nodes      */
+/* first (solid_value), then the x sides, then the y sides over the    */
+/* extended x range (so corners take the y rule applied to the x       */
+/* ghosts).  Periodic sides wrap; wall sides use the wetting ghost      */
+/* (wetting != 0) or the mirror value (wetting == 0).                  */
 /* ------------------------------------------------------------------ */
 #define PADI(st, i, j) ((size_t)((j) + 1) * (size_t)((st)->nx + 2) + (size_t)((i) + 1))
+
+/* Node index of (i, j) wrapped across periodic sides, or -1 beyond a wall. */
+static long node_at(const ostate *st, int i, int j)
+{
+    if (i < 0 || i >= st->nx) {
+        if (st->P.bc[O_LEFT] != O_PERIODIC) return -1;
+        i = (i + st->nx) % st->nx;
+    }
+    if (j < 0 || j >= st->ny) {
+        if (st->P.bc[O_BOTTOM] != O_PERIODIC) return -1;
+        j = (j + st->ny) % st->ny;
+    }
+    return (long)j * st->nx + i;
+}
+
+/* Value a solid node (i, j) shows to the stencils.  The paper states the
+ * wetting condition for plane walls only (Eqs. (49)-(50)); for obstacles the
+ * reading is neutral wetting: the mean of the field over the fluid nodes
+ * among the four axis neighbours, or, if there are none, over the fluid
+ * diagonal neighbours (0 where no fluid node is adjacent: no fluid stencil
+ * reaches it).  Next to a plane wall of solid nodes this is the mirror value,
+ * the theta = 90 degrees ghost of Eq. (50). */
+static double solid_value(const ostate *st, const double *a, int i, int j)
+{
+    for (int k0 = 1; k0 <= 5; k0 += 4) {
+        double s = 0.0;
+        int c = 0;
+        for (int k = k0; k < k0 + 4; ++k) {
+            const long q = node_at(st, i + CX[k], j + CY[k]);
+            if (q >= 0 && !st->solid[q]) {
+                s += a[q];
+                ++c;
+            }
+        }
+        if (c > 0) return s / c;
+    }
+    return 0.0;
+}
 
 static void fill_pad(ostate *st, const double *a, double *pad, int wetting)
 {
     const int nx = st->nx, ny = st->ny;
     const oracle_params *P = &st->P;
     for (int j = 0; j < ny; ++j)
-        for (int i = 0; i < nx; ++i) pad[PADI(st, i, j)] = a[(size_t)j * nx + i];
+        for (int i = 0; i < nx; ++i) {
+            const size_t n = (size_t)j * nx + i;
+            pad[PADI(st, i, j)] = (st->solid && st->solid[n]) ? solid_value(st, a, i, j) : a[n];
+        }
     for (int j = 0; j < ny; ++j) {
-        const double *row = a + (size_t)j * nx;
+        const double c0 = pad[PADI(st, 0, j)], c1 = pad[PADI(st, 1, j)];
+        const double e0 = pad[PADI(st, nx - 1, j)], e1 = pad[PADI(st, nx - 2, j)];
         if (P->bc[O_LEFT] == O_PERIODIC) {
-            pad[PADI(st, -1, j)] = row[nx - 1];
-            pad[PADI(st, nx, j)] = row[0];
+            pad[PADI(st, -1, j)] = e0;
+            pad[PADI(st, nx, j)] = c0;
         } else {
-            pad[PADI(st, -1, j)] = wetting ? wall_ghost(P, row[0], row[1], st->cos_t[O_LEFT], &st->wet_flag) : row[0];
-            pad[PADI(st, nx, j)] = wetting ? wall_ghost(P, row[nx - 1], row[nx - 2], st->cos_t[O_RIGHT], &st->wet_flag) : row[nx - 1];
+            pad[PADI(st, -1, j)] = wetting ? wall_ghost(P, c0, c1, st->cos_t[O_LEFT], &st->wet_flag) : c0;
+            pad[PADI(st, nx, j)] = wetting ? wall_ghost(P, e0, e1, st->cos_t[O_RIGHT], &st->wet_flag) : e0;
         }
     }
     for (int i = -1; i <= nx; ++i) {
@@ -384,6 +434,18 @@ static void phase_pass(ostate *st)
 
 }
 
+/* Every per-node quantity of a solid node is zero (it carries no fluid). */
+static void zero_solid(ostate *st)
+{
+    double *arrs[] = {st->phi, st->gpx, st->gpy, st->lap, st->mu, st->Dx, st->Dy, st->lam, st->nxv,
+                      st->nyv, st->rho, st->ux, st->uy, st->p, st->mcx, st->mcy, st->Fx, st->Fy,
+                      st->s78, st->cur[0], st->cur[1], st->cur[2], st->cur[3], st->cur[4],
+                      st->dt[0], st->dt[1], st->dt[2], st->dt[3], st->dt[4]};
+    for (long n = 0; n < st->N; ++n)
+        if (st->solid[n])
+            for (size_t k = 0; k < sizeof(arrs) / sizeof(arrs[0]); ++k) arrs[k][n] = 0.0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Macroscopic pass at the current time t.  Fills phi, gradients, mu,  */
 /* D, rho, m^{phi C}, F, u, p, the per-node viscous rate and the       */
@@ -467,6 +529,7 @@ static void macro_pass(ostate *st)
         st->Fx[n] = Fx;
         st->Fy[n] = Fy;
     }
+    if (st->solid) zero_solid(st);
 }
 
 static void gather_node_input(const ostate *st, long n, double in[20])
@@ -498,6 +561,10 @@ static void collide(ostate *st)
     const oracle_params *P = &st->P;
 #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
+        if (st->solid && st->solid[n]) {
+            for (int i = 0; i < 9; ++i) st->fs[i][n] = st->gs[i][n] = 0.0;
+            continue;
+        }
         double in[20], mfeq[9], mR[9], mgeq[9], mF[9];
         gather_node_input(st, n, in);
         node_moments(P, in, mfeq, mR, mgeq, mF);
@@ -539,8 +606,9 @@ static void collide(ostate *st)
 }
 
 /* Streaming x_i(x + c_i, t+1) = x_i*(x, t), written as a pull; a link whose
- * upstream node x - c_i lies beyond a wall takes the reflected population
- * x_{opp(i)}*(x, t) (half-way bounce-back, Sec. 4). */
+ * upstream node x - c_i lies beyond a wall, or is a solid node, takes the
+ * reflected population x_{opp(i)}*(x, t) (half-way bounce-back, Sec. 4).
+ * Solid nodes hold no populations (zero). */
 static void stream_pull(ostate *st, double *const *src, double *const *dst)
 {
     const int nx = st->nx, ny = st->ny;
@@ -549,6 +617,10 @@ static void stream_pull(ostate *st, double *const *src, double *const *dst)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             const size_t n = (size_t)y * nx + x;
+            if (st->solid && st->solid[n]) {
+                for (int i = 0; i < 9; ++i) dst[i][n] = 0.0;
+                continue;
+            }
             for (int i = 0; i < 9; ++i) {
                 int sx = x - CX[i], sy = y - CY[i];
                 int wall = 0;
@@ -560,6 +632,7 @@ static void stream_pull(ostate *st, double *const *src, double *const *dst)
                     if (P->bc[O_BOTTOM] == O_PERIODIC) sy = (sy + ny) % ny;
                     else wall = 1;
                 }
+                if (!wall && st->solid && st->solid[(size_t)sy * nx + sx]) wall = 1;
                 dst[i][n] = wall ? src[OPP[i]][n] : src[i][(size_t)sy * nx + sx];
             }
         }
@@ -571,8 +644,9 @@ static void stream_pull(ostate *st, double *const *src, double *const *dst)
 /*       viscous rate s_2 = s_g^7 of the node;                          */
 /*  S_m: rms of d rho/dt + div(rho u + m^{phi C}), d rho/dt by explicit */
 /*       Euler against phi(t-1), the divergence by Eq. (C.9).           */
-/* Both are averaged over the nodes not adjacent to a wall (their       */
-/* stencils would reach beyond the wall).  Requires macro_pass() first. */
+/* Both are averaged over the fluid nodes not adjacent to a wall or a   */
+/* solid node (their stencils would reach beyond the boundary); sums    */
+/* and maxima run over the fluid nodes.  Requires macro_pass() first.   */
 /* out: t, sum phi, D_u^rms, S_m^rms, max|u|, non-finite count,         */
 /*      number of averaged nodes, 0                                     */
 /* ------------------------------------------------------------------ */
@@ -584,6 +658,7 @@ static void diagnostics(ostate *st, double out[O_NDIAG])
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             const long n = (long)y * nx + x;
+            if (st->solid && st->solid[n]) continue;
             sphi += st->phi[n];
             const double um2 = st->ux[n] * st->ux[n] + st->uy[n] * st->uy[n];
             if (!isfinite(st->phi[n]) || !isfinite(um2)) nbad += 1.0;
@@ -591,6 +666,14 @@ static void diagnostics(ostate *st, double out[O_NDIAG])
             if ((P->bc[O_LEFT] == O_WALL && (x == 0 || x == nx - 1)) ||
                 (P->bc[O_BOTTOM] == O_WALL && (y == 0 || y == ny - 1)))
                 continue;
+            if (st->solid) {
+                int near = 0;
+                for (int k = 1; k < 9; ++k) {
+                    const long q = node_at(st, x + CX[k], y + CY[k]);
+                    if (q >= 0 && st->solid[q]) near = 1;
+                }
+                if (near) continue;
+            }
             /* tr S, Eq. (35): tr sum c c (g - g^eq) = [(m1-m1eq) + 4 (m0-m0eq)]/3,
              * tr M_2F = (mF1 + 4 mF0)/3 */
             double in[20], mfeq[9], mR[9], mgeq[9], mF[9], m[9];
@@ -649,6 +732,7 @@ void oracle_destroy(ostate *st)
                       st->Dx, st->Dy, st->lam, st->nxv, st->nyv, st->rho, st->ux, st->uy, st->p,
                       st->mcx, st->mcy, st->Fx, st->Fy, st->s78};
     for (size_t k = 0; k < sizeof(arrs) / sizeof(arrs[0]); ++k) free(arrs[k]);
+    free(st->solid);
     free(st);
 }
 
@@ -771,11 +855,12 @@ int oracle_init_fields(ostate *st, const double *phi0, const double *ux0, const 
         in[7] = my;
         double mfeq[9], mR[9], mgeq[9], mF[9];
         node_moments(P, in, mfeq, mR, mgeq, mF);
+        const int solid = st->solid && st->solid[n];
         for (int i = 0; i < 9; ++i) {
             double sf = 0.0, sg = 0.0;
             for (int k = 0; k < 9; ++k) { sf += MINV[i][k] * mfeq[k]; sg += MINV[i][k] * mgeq[k]; }
-            st->f[i][n] = sf;
-            st->g[i][n] = sg;
+            st->f[i][n] = solid ? 0.0 : sf;
+            st->g[i][n] = solid ? 0.0 : sg;
         }
     }
     for (int k = 0; k < 5; ++k) memset(st->hist[k], 0, sizeof(double) * N);
@@ -877,6 +962,23 @@ int oracle_set_fields(ostate *st, int32_t which, const double *in)
 
 long oracle_time(const ostate *st) { return st ? st->t : -1; }
 
+/* Mark solid nodes (mask [ny][nx], nonzero = solid; NULL removes them).
+ * Takes effect from the next call; set it before oracle_init_fields so that
+ * the initial state already holds no populations at solid nodes. */
+int oracle_set_solid(ostate *st, const uint8_t *mask)
+{
+    if (!st) return O_EINVAL;
+    if (!mask) {
+        free(st->solid);
+        st->solid = NULL;
+        return O_OK;
+    }
+    if (!st->solid) st->solid = (unsigned char *)malloc((size_t)st->N);
+    if (!st->solid) return O_ENOMEM;
+    for (long n = 0; n < st->N; ++n) st->solid[n] = mask[n] ? 1 : 0;
+    return O_OK;
+}
+
 /* ------------------------------------------------------------------ */
 /* Test hooks (node-level pieces, so tests can pin them to the paper). */
 /* ------------------------------------------------------------------ */
@@ -917,6 +1019,17 @@ int oracle_grad_lap(int nx, int ny, const double *field, double *gx, double *gy,
     fill_pad(&tmp, field, pad, 0);
     stencil(&tmp, pad, gx, gy, lap);
     free(pad);
+    return O_OK;
+}
+
+/* The padded field (nx+2) x (ny+2), x fastest, node (i, j) at (i+1, j+1),
+ * as the stencils of the last macro pass saw it: which = 0 phi (wetting
+ * ghosts), 1 mu_phi (mirror ghosts; Cahn-Hilliard only). */
+int oracle_padded(ostate *st, int32_t which, double *out)
+{
+    if (!st || !out || which < 0 || which > 1) return O_EINVAL;
+    if (which == 1 && st->P.phase_model != O_CH) return O_EINVAL;
+    memcpy(out, which ? st->padmu : st->pad, sizeof(double) * (size_t)(st->nx + 2) * (st->ny + 2));
     return O_OK;
 }
 

@@ -141,6 +141,7 @@ class Case:
     p: np.ndarray | None = None
     steps: int = 100
     notes: dict = field(default_factory=dict)
+    solid: np.ndarray | None = None  # [ny][nx] bool, solid obstacle nodes
 
 
 def _coords(nx: int, ny: int):
@@ -380,6 +381,39 @@ def dam_break(nx: int = 4096, ny: int = 2048, col_w: int = 1024, col_h: int | No
                        tanh_profile(W - np.sqrt((X - a_x + W) ** 2 + (Y - a_y + W) ** 2), W, 1.0, 0.0),
                        1.0)))
     return Case("dam_break", prm, phi, steps=steps)
+
+
+# --------------------------------------------------------------------------
+# Sec. 4.5, last case: dam break over a trapezoidal obstacle on the bottom wall.
+# The paper gives the obstacle's height (a/2) and position (centred at Lx/2)
+# and shows its shape only in a figure; reading: an isosceles trapezoid with
+# 45-degree flanks and a top of width a/2 (base 3a/2).  Solid nodes are those
+# whose centre (i + 1/2, j + 1/2) lies inside it.
+# --------------------------------------------------------------------------
+def trapezoid_mask(nx: int, ny: int, xc: float, height: float, top: float,
+                   slope: float = 1.0) -> np.ndarray:
+    """Solid nodes of a trapezoid standing on the bottom wall: centred at
+    x = xc, `height` tall, `top` wide at the top, flanks of dx/dy = slope."""
+    X, Y = _coords(nx, ny)
+    half = 0.5 * top + slope * (height - Y)
+    return (Y <= height) & (np.abs(X - xc) <= half)
+
+
+def disc_mask(nx: int, ny: int, xc: float, yc: float, r: float) -> np.ndarray:
+    X, Y = _coords(nx, ny)
+    return (X - xc) ** 2 + (Y - yc) ** 2 <= r * r
+
+
+def dam_break_obstacle(nx: int = 4096, ny: int = 2048, precision: int = PREC_FP32,
+                       steps: int = 2000, **kw) -> Case:
+    """Dam break in a 4a x 2a chamber (a = nx/4): a x a water column at the
+    left, trapezoidal obstacle of height a/2 at x = Lx/2 (the reading above)."""
+    a = nx // 4
+    case = dam_break(nx=nx, ny=ny, col_w=a, col_h=a, precision=precision, steps=steps, **kw)
+    solid = trapezoid_mask(nx, ny, 0.5 * nx, 0.5 * a, 0.5 * a)
+    phi = np.where(solid, case.params.phiB, case.phi)
+    return Case("dam_break_obstacle", case.params, phi, steps=steps, solid=solid,
+                notes={"a": a, "obstacle": "trapezoid h=a/2 top=a/2 45deg at Lx/2"})
 
 
 # --------------------------------------------------------------------------
