@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--adjoint-precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--adjoint-only", action="store_true",
                     help="time only the adjoint against the forward pass (profiling)")
+    ap.add_argument("--obstacle-only", action="store_true",
+                    help="time only the dam break over the obstacle, beside the same chamber "
+                         "without it on both fused kernels (profiling)")
     return ap.parse_args()
 
 
@@ -292,6 +295,50 @@ def adjoint_timing(args, torch):
 
 
 # ---------------------------------------------------------------------------
+def obstacle_timing(args, torch, pk, stream, barrier, max_over_ranks, world, peak, compare=False):
+    """The dam break over the trapezoidal obstacle, 4096 x 2048 (a = 1024,
+    height a/2 at Lx/2), FP32, Allen-Cahn, through the obstacle passes (phi,
+    fill, node update: 3 launches a step); 5 x K steps after W warm-up steps,
+    CUDA events on the simulation's stream.  compare: also the same chamber
+    without the obstacle on the TMA and on the register-pipelined kernel."""
+    db = W.dam_break_obstacle(nx=4096, ny=2048, precision=W.PREC_FP32)
+    nodes = db.params.nx * db.params.ny
+    nst = 5 * args.steps
+
+    def run(params, solid):
+        sim = pk.Simulation(params, stream=stream)
+        if solid is not None:
+            sim.set_solid(solid)
+        sim.init_fields(db.phi)
+        sim.step(args.warmup)
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(nst)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        gb = sim.device_bytes / 1e9
+        sim.close()
+        return ms, gb
+
+    oms, gb = run(db.params, db.solid)
+    out = {"dam_break_obstacle_4096x2048": {
+        "value": whole_job_mlups(world, nodes, nst, oms / 1e3), "unit": UNIT, "steps": nst,
+        "ms_per_step": oms / nst, "solid_fraction": float(db.solid.mean()), "launches_per_step": 3,
+        "frac_of_fused_bytes": PRECISIONS["fp32"][2] * nodes * nst / (oms / 1e3) / 1e9 / peak,
+        "l2": f"state {gb:.2f} GB > L2"}}
+    if compare:
+        for name, flags in (("no_obstacle_tma", 0), ("no_obstacle_register_kernel", pk.LBM_FLAG_NO_TMA)):
+            ms, _ = run(db.params.with_(flags=flags), None)
+            out[name] = {"value": whole_job_mlups(world, nodes, nst, ms / 1e3), "unit": UNIT,
+                         "ms_per_step": ms / nst}
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -326,7 +373,6 @@ def main():
 
     prec, dtype, bytes_per_lu = PRECISIONS[args.precision]
     n = args.n
-    case = W.rti_multimode(n, precision=prec)
     N = n * n
 
     def barrier():
@@ -338,6 +384,12 @@ def main():
 
     stream = torch.cuda.current_stream(dev)
     peak, peak_src = measured_peak()
+    if args.obstacle_only:
+        res = obstacle_timing(args, torch, pk, stream, barrier, max_over_ranks, world, peak, compare=True)
+        if rank == 0:
+            print(json.dumps({"metric": "obstacle step MLUPS", "obstacle_workloads": res}), flush=True)
+        return
+    case = W.rti_multimode(n, precision=prec)
 
     def timed_steps(params, label, per_lu_bytes, phi0=None):
         """W warm-up steps, then K steps timed with CUDA events on the
@@ -422,6 +474,10 @@ def main():
                 "l2": f"state {ssim.device_bytes / 1e9:.2f} GB > L2"}
             ssim.close()
 
+    obstacle = None
+    if args.precision == "fp32" and not args.no_storage_compare:
+        obstacle = obstacle_timing(args, torch, pk, stream, barrier, max_over_ranks, world, peak)
+
     # ---- the Cahn-Hilliard alternative on the same workload (phi in [-1, 1])
     models = None
     if args.precision == "fp32" and not args.no_storage_compare:
@@ -464,7 +520,7 @@ def main():
                            "l2": f"inputs larger than L2 (device state {state_gb:.1f} GB)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps, "clocks": clk, "storage_variants": storage,
-                "wetting_workloads": wetting, "model_variants": models,
+                "wetting_workloads": wetting, "obstacle_workloads": obstacle, "model_variants": models,
                 "adjoint": adjoint}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -222,6 +222,30 @@ int lbm_fields_noalloc(lbm_handle *h, int32_t which, double *out);
  * LBM_EINVAL. */
 int lbm_set_fields(lbm_handle *h, int32_t which, const double *in);
 
+/*
+ * Solid obstacles inside the grid (the dam break over an obstacle, Sec. 4.5).
+ *  solid  host [ny][nx] bytes, nonzero = solid node (read during the call);
+ *         NULL or all zero removes the obstacles.
+ * A solid node takes no part in the flow.  A link whose upstream node is
+ * solid reflects like a wall link (half-way bounce-back, Sec. 4), so the
+ * solid surface lies half-way between a solid node and its fluid neighbour.
+ * The paper states the wetting condition for plane walls only (Eqs.
+ * (49)-(50)); at a solid node the isotropic stencils see the neutral-wetting
+ * value of phi (and of mu_phi for Cahn-Hilliard): the mean over its fluid
+ * axis neighbours, or, with none, over its fluid diagonal neighbours.  Next
+ * to a plane of solid nodes this is the 90-degree wall ghost (the mirror
+ * value).  Every field of lbm_fields is zero at solid nodes; the
+ * diagnostics sum over fluid nodes and average over fluid nodes without a
+ * reflecting link.
+ * Takes effect from the next call; call it before lbm_init_fields so that
+ * the initial state holds no populations at solid nodes.  With obstacles the
+ * step runs as four passes over the grid (five for Cahn-Hilliard) instead of
+ * the fused kernels.  Device memory: a 2-byte link word per node and two
+ * work planes of the arithmetic type.  The adjoint entry points return
+ * LBM_EUNSUPPORTED while obstacles are set.
+ */
+int lbm_set_solid(lbm_handle *h, const uint8_t *solid);
+
 /* Number of time steps taken since lbm_init_fields. */
 int64_t lbm_time(const lbm_handle *h);
 

@@ -32,7 +32,7 @@ LBM_FLAG_NO_TMA = 1
 DIAG_KEYS = ("t", "sum_phi", "Du_rms", "Sm_rms", "umax", "nonfinite", "n_avg", "reserved")
 
 EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_fields", "lbm_fields_region",
-            "lbm_fields_noalloc", "lbm_set_fields",
+            "lbm_fields_noalloc", "lbm_set_fields", "lbm_set_solid",
             "lbm_time", "lbm_device_bytes", "lbm_destroy", "lbm_last_error",
             "lbm_state_bytes", "lbm_snapshot", "lbm_restore", "lbm_adjoint_seed", "lbm_adjoint_step",
             "lbm_adjoint_init", "lbm_adjoint_gravity")
@@ -86,6 +86,7 @@ def load(path: str | None = None):
                                     C.c_int32, dp]
     L.lbm_set_fields.argtypes = [C.c_void_p, C.c_int32, dp]
     L.lbm_fields_noalloc.argtypes = [C.c_void_p, C.c_int32, dp]
+    L.lbm_set_solid.argtypes = [C.c_void_p, C.POINTER(C.c_uint8)]
     L.lbm_time.argtypes = [C.c_void_p]
     L.lbm_time.restype = C.c_int64
     L.lbm_device_bytes.argtypes = [C.c_void_p]
@@ -180,6 +181,12 @@ def lbm_fields_noalloc(h, which: int, out: np.ndarray):
 
 def lbm_set_fields(h, which: int, arr: np.ndarray):
     _check(load().lbm_set_fields(h, int(which), _dptr(arr)), h)
+
+
+def lbm_set_solid(h, solid: np.ndarray | None):
+    """Solid obstacle nodes: [ny][nx] uint8 (nonzero = solid), or None."""
+    ptr = None if solid is None else solid.ctypes.data_as(C.POINTER(C.c_uint8))
+    _check(load().lbm_set_solid(h, ptr), h)
 
 
 def lbm_time(h) -> int:
@@ -300,6 +307,17 @@ class Simulation:
         if a.shape != (self.ny, self.nx):
             raise ValueError(f"field shape {a.shape} != {(self.ny, self.nx)}")
         return a
+
+    def set_solid(self, solid):
+        """Solid obstacle nodes ([ny][nx], nonzero = solid; None removes them).
+        Call before init_fields."""
+        if solid is None:
+            lbm_set_solid(self._h, None)
+            return
+        m = np.ascontiguousarray(np.asarray(solid) != 0, dtype=np.uint8)
+        if m.shape != (self.ny, self.nx):
+            raise ValueError(f"mask shape {m.shape} != {(self.ny, self.nx)}")
+        lbm_set_solid(self._h, m)
 
     def init_fields(self, phi, ux=None, uy=None, p=None):
         arrs = [self._field(x) for x in (phi, ux, uy, p)]

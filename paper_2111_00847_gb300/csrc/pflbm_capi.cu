@@ -56,6 +56,10 @@ struct lbm_handle {
   bool have_adj = false;
   double* gacc = nullptr;  // accumulated dJ/dG
   bool init_u_zero = true; // the last lbm_init_fields had u = 0
+  // solid obstacles (lbm_set_solid): reflecting links per node and the phi /
+  // mu_phi work planes of the obstacle passes
+  uint16_t* dobs = nullptr;
+  void* obs_planes = nullptr;
 };
 
 static std::string g_create_error;
@@ -237,6 +241,7 @@ static Phys<T> make_phys(const lbm_handle* h) {
     P.dv_is[set] = T(1.0 / h->dv_s[set]);
   }
   P.dv_c0 = T(h->dv_c0);
+  P.obs = h->dobs;
   return P;
 }
 
@@ -285,6 +290,17 @@ static int check_device_flag(lbm_handle* h) {
   return LBM_OK;
 }
 
+// One pass of the fused kernel in a mode, or, with solid obstacles, the
+// obstacle passes (pflbm_obstacle.cuh).
+template <class C>
+static cudaError_t launch_mode(lbm_handle* h, int mode, const Phys<typename C::value_t>& P,
+                               const Bufs<typename C::value_t>& B) {
+  using T = typename C::value_t;
+  if (!h->dobs) return launch_march<C>(h->prm.phase_model, mode, P, B, h->stream);
+  T* phis = (T*)h->obs_planes;
+  return launch_obs<C>(h->prm.phase_model, mode, P, B, phis, phis + h->plane, h->unit_rates, h->stream);
+}
+
 template <class C>
 static int run_macro(lbm_handle* h) {
   using T = typename C::value_t;
@@ -293,7 +309,7 @@ static int run_macro(lbm_handle* h) {
   const Phys<T> P = make_phys<T>(h);
   Bufs<T> B = bufs_now<T>(h);
   B.macro = (T*)h->macro;
-  CUDA_TRY(h, launch_march<C>(h->prm.phase_model, MODE_MACRO, P, B, h->stream));
+  CUDA_TRY(h, launch_mode<C>(h, MODE_MACRO, P, B));
   return LBM_OK;
 }
 
@@ -331,7 +347,9 @@ static int do_step(lbm_handle* h, int64_t n) {
     Bufs<T> B = bufs_now<T>(h);
     B.phi_prev = due ? (T*)h->phi_prev : nullptr;
     cudaError_t e = cudaErrorNotSupported;
-    if (h->use_tma && h->prm.phase_model == LBM_AC)
+    if (h->dobs)
+      e = launch_mode<C>(h, MODE_STEP, P, B);
+    else if (h->use_tma && h->prm.phase_model == LBM_AC)
       e = launch_step_tma<C>(P, B, h->derr, h->unit_rates, h->stream);
     else if (h->use_tma && h->prm.phase_model == LBM_CH)
       e = launch_step_tma_ch<C>(P, B, h->derr, h->unit_rates, h->stream);
@@ -378,7 +396,7 @@ static int do_init(lbm_handle* h, const double* phi, const double* ux, const dou
   if (p) { CUDA_TRY(h, cudaMemcpyAsync(d, p, N * sizeof(double), cudaMemcpyHostToDevice, h->stream)); B.ip = d; d += N; }
   if constexpr (!C::dev) {
     // equilibria per node into the spare buffers, then scatter to the pull layout
-    CUDA_TRY(h, launch_march<C>(h->prm.phase_model, MODE_INIT, P, B, h->stream));
+    CUDA_TRY(h, launch_mode<C>(h, MODE_INIT, P, B));
     CUDA_TRY(h, launch_unstream<T>(P, (const T*)h->pops[0][1 - h->cur], (T*)h->pops[0][h->cur], h->stream));
     CUDA_TRY(h, launch_unstream<T>(P, (const T*)h->pops[1][1 - h->cur], (T*)h->pops[1][h->cur], h->stream));
   } else {
@@ -388,7 +406,7 @@ static int do_init(lbm_handle* h, const double* phi, const double* ux, const dou
     T* gs = scratch + 9 * h->plane;
     B.fout = scratch;
     B.gout = gs;
-    cudaError_t e = launch_march<C>(h->prm.phase_model, MODE_INIT, P, B, h->stream);
+    cudaError_t e = launch_mode<C>(h, MODE_INIT, P, B);
     if (e == cudaSuccess) e = launch_restream<C>(P, scratch, h->pops[0][h->cur], 0, h->stream);
     if (e == cudaSuccess) e = launch_restream<C>(P, gs, h->pops[1][h->cur], 1, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -398,7 +416,7 @@ static int do_init(lbm_handle* h, const double* phi, const double* ux, const dou
   // history := chi(0), and phi(t-1) := phi(0)
   Bufs<T> Bh = bufs_now<T>(h);
   Bh.phi_prev = (T*)h->phi_prev;
-  CUDA_TRY(h, launch_march<C>(h->prm.phase_model, MODE_HIST, P, Bh, h->stream));
+  CUDA_TRY(h, launch_mode<C>(h, MODE_HIST, P, Bh));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   h->t = 0;
   std::memset(h->diag, 0, sizeof(h->diag));
@@ -644,6 +662,47 @@ int lbm_set_fields(lbm_handle* h, int32_t which, const double* in) {
   PFLBM_DISPATCH(h, do_set_fields, h, which, in);
 }
 
+int lbm_set_solid(lbm_handle* h, const uint8_t* solid) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  long long nsolid = 0;
+  const long long N = (long long)h->nx * h->ny;
+  if (solid)
+    for (long long n = 0; n < N; ++n) nsolid += solid[n] != 0;
+  if (nsolid == 0) {  // no obstacles: back to the fused kernels
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    dev_free(h, h->dobs);
+    dev_free(h, h->obs_planes);
+    h->dobs = nullptr;
+    h->obs_planes = nullptr;
+    return LBM_OK;
+  }
+  if (!h->dobs) {
+    h->dobs = (uint16_t*)dev_alloc(h, (size_t)N * sizeof(uint16_t));
+    h->obs_planes = dev_alloc(h, 2 * (size_t)h->plane * h->esize);
+    if (!h->dobs || !h->obs_planes) {
+      dev_free(h, h->dobs);
+      dev_free(h, h->obs_planes);
+      h->dobs = nullptr;
+      h->obs_planes = nullptr;
+      return fail(h, LBM_ENOMEM, "obstacle planes");
+    }
+    CUDA_TRY(h, cudaMemsetAsync(h->obs_planes, 0, 2 * (size_t)h->plane * h->esize, h->stream));
+  }
+  // the byte mask goes through the staging buffer (N bytes <= N doubles)
+  int rc = ensure_stage(h, 1);
+  if (rc) return rc;
+  CUDA_TRY(h, cudaMemcpyAsync(h->dstage, solid, (size_t)N, cudaMemcpyHostToDevice, h->stream));
+  if (h->prec == LBM_FP64) {
+    const Phys<double> P = make_phys<double>(h);
+    CUDA_TRY(h, launch_obs_links<double>(P, (const unsigned char*)h->dstage, h->dobs, h->stream));
+  } else {
+    const Phys<float> P = make_phys<float>(h);
+    CUDA_TRY(h, launch_obs_links<float>(P, (const unsigned char*)h->dstage, h->dobs, h->stream));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
 int64_t lbm_time(const lbm_handle* h) { return h ? h->t : -1; }
 
 int64_t lbm_device_bytes(const lbm_handle* h) { return h ? h->bytes : 0; }
@@ -786,6 +845,7 @@ static int ensure_adjoint(lbm_handle* h) {
 }
 
 static int adjoint_supported(lbm_handle* h) {
+  if (h->dobs) return fail(h, LBM_EUNSUPPORTED, "the adjoint does not cover solid obstacles");
   if (h->prm.phase_model != LBM_AC)
     return fail(h, LBM_EUNSUPPORTED, "the adjoint covers the Allen-Cahn phase field only");
   if (h->prec != LBM_FP64 && h->prec != LBM_FP32)

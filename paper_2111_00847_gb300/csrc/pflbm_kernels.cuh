@@ -90,7 +90,12 @@ struct Phys {
   // 1 / (1 + sum_i r_i) that makes a node's decoded populations sum to phi.
   T dv_r[2][2], dv_s[2], dv_is[2], dv_c0;
   int seg_rows;  // rows per block segment of the TMA step on small grids (set by its launcher)
+  // Solid obstacles (nullptr: none).  Per node of the dense [ny][nx] grid:
+  // bit i-1 (i = 1..8) set when link i reflects, i.e. its upstream node
+  // x - c_i is solid or lies beyond a wall; bit OBS_SOLID set at solid nodes.
+  const uint16_t* obs;
 };
+constexpr int OBS_SOLID = 8;
 
 // Population sets are addressed in bytes through a storage codec: plane 0
 // of a row block holds B0-byte elements, planes 1..8 BI-byte elements, and
@@ -232,6 +237,37 @@ __device__ __forceinline__ void pull9(const void* buf_, const Phys<typename C::v
     out[6] = (bxp || bym) ? pop_ld<C>(buf, P, set, 8, x, r) : pop_ld<C>(buf, P, set, 6, xp, ym);
     out[7] = (bxp || byp) ? pop_ld<C>(buf, P, set, 5, x, r) : pop_ld<C>(buf, P, set, 7, xp, yp);
     out[8] = (bxm || byp) ? pop_ld<C>(buf, P, set, 6, x, r) : pop_ld<C>(buf, P, set, 8, xm, yp);
+  }
+}
+
+// The same pull on a grid with solid obstacles: a link flagged in P.obs
+// reflects (half-way bounce-back at the solid surface, as at a wall); the
+// others wrap across periodic sides.  A solid node sees no populations.
+template <class C>
+__device__ __forceinline__ void pull9_obs(const void* buf_, const Phys<typename C::value_t>& P, int set, int x,
+                                          int r, typename C::value_t out[9]) {
+  using T = typename C::value_t;
+  const unsigned m = P.obs[(long long)r * P.nx + x];
+  const unsigned char* buf = static_cast<const unsigned char*>(buf_);
+  constexpr int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  constexpr int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  constexpr int op[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+  if ((m >> OBS_SOLID) & 1u) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) out[i] = T(0);
+    return;
+  }
+  out[0] = pop_ld<C>(buf, P, set, 0, x, r);
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    if ((m >> (i - 1)) & 1u) {
+      out[i] = pop_ld<C>(buf, P, set, op[i], x, r);
+    } else {
+      int sx = x - cx[i], sy = r - cy[i];
+      sx = sx < 0 ? sx + P.nx : (sx >= P.nx ? sx - P.nx : sx);
+      sy = sy < 0 ? sy + P.ny : (sy >= P.ny ? sy - P.ny : sy);
+      out[i] = pop_ld<C>(buf, P, set, i, sx, sy);
+    }
   }
 }
 
@@ -1622,15 +1658,19 @@ __global__ void k_pull(const Phys<T> P, const T* __restrict__ in, T* __restrict_
   const int y = blockIdx.y;
   if (x >= P.nx) return;
   T v[9];
-  pull9<PopPlain<T>>(in, P, 0, x, y, v);
+  if (P.obs)
+    pull9_obs<PopPlain<T>>(in, P, 0, x, y, v);
+  else
+    pull9<PopPlain<T>>(in, P, 0, x, y, v);
   T* o = out + ix(P, 9, 0, x, y);
 #pragma unroll
   for (int i = 0; i < 9; ++i) o[i * P.pitch] = v[i];
 }
 
 // Inverse of the pull: the population node x sees in direction i came from
-// x - c_i (or, beyond a wall, from x itself in direction opp(i)).  Every
-// destination entry is written exactly once.
+// x - c_i (or, beyond a wall or from a solid node, from x itself in
+// direction opp(i)).  Every destination entry a fluid node pulls is written
+// exactly once; solid nodes scatter nothing (no fluid node reads them).
 template <typename T>
 __global__ void k_unstream(const Phys<T> P, const T* __restrict__ in, T* __restrict__ out) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1639,10 +1679,12 @@ __global__ void k_unstream(const Phys<T> P, const T* __restrict__ in, T* __restr
   const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
   const int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
   const int op[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+  const unsigned m = P.obs ? P.obs[(long long)y * P.nx + x] : 0u;
+  if ((m >> OBS_SOLID) & 1u) return;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     int sx = x - cx[i], sy = y - cy[i];
-    bool wall = false;
+    bool wall = i > 0 && ((m >> (i - 1)) & 1u);
     if (sx < 0 || sx >= P.nx) { if (P.wall_x) wall = true; else sx = (sx + P.nx) % P.nx; }
     if (sy < 0 || sy >= P.ny) { if (P.wall_y) wall = true; else sy = (sy + P.ny) % P.ny; }
     const T val = in[ix(P, 9, i, x, y)];
@@ -1666,15 +1708,20 @@ __global__ void k_pull_export(const Phys<typename C::value_t> P, const void* __r
   const int yy = blockIdx.y;
   if (xx >= w) return;
   T v[9];
-  pull9<C>(in, P, set, x0 + xx, y0 + yy, v);
+  if (P.obs) {
+    pull9_obs<C>(in, P, set, x0 + xx, y0 + yy, v);
+    if ((P.obs[(long long)(y0 + yy) * P.nx + x0 + xx] >> OBS_SOLID) & 1u) add = 0.0;  // solid: zero
+  } else {
+    pull9<C>(in, P, set, x0 + xx, y0 + yy, v);
+  }
   out[(long long)yy * w + xx] = double(v[k]) + add;
 }
 
 // Deviation storage: the inverse of the pull, node by node.  Slot j of
 // node s receives the value node s + c_j pulls in direction j, or, where
-// s + c_j lies beyond a wall, the value s itself pulls in direction opp(j);
-// the node's nine slots are then encoded together (for f with the node's
-// zeroth moment kept exact).
+// s + c_j lies beyond a wall or is solid, the value s itself pulls in
+// direction opp(j); the node's nine slots are then encoded together (for f
+// with the node's zeroth moment kept exact).  Solid nodes store zeros.
 template <class C>
 __global__ void k_restream(const Phys<typename C::value_t> P, const typename C::value_t* __restrict__ in,
                            void* __restrict__ out, int set) {
@@ -1686,10 +1733,18 @@ __global__ void k_restream(const Phys<typename C::value_t> P, const typename C::
   const int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
   const int op[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
   T v[9];
+  const unsigned m = P.obs ? P.obs[(long long)y * P.nx + x] : 0u;
+  if ((m >> OBS_SOLID) & 1u) {
+#pragma unroll
+    for (int j = 0; j < 9; ++j) v[j] = T(0);
+    store_pops<C>(P, out, set, x, y, v, T(0), set == 0);
+    return;
+  }
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
     int tx = x + cx[j], ty = y + cy[j];
-    bool wall = false;
+    // link opp(j) of s starts at s + c_j
+    bool wall = j > 0 && ((m >> (op[j] - 1)) & 1u);
     if (tx < 0 || tx >= P.nx) { if (P.wall_x) wall = true; else tx = (tx + P.nx) % P.nx; }
     if (ty < 0 || ty >= P.ny) { if (P.wall_y) wall = true; else ty = (ty + P.ny) % P.ny; }
     v[j] = wall ? in[ix(P, 9, op[j], x, y)] : in[ix(P, 9, j, tx, ty)];
@@ -1698,13 +1753,14 @@ __global__ void k_restream(const Phys<typename C::value_t> P, const typename C::
 }
 
 // plane k of a set of NP interleaved planes -> dense doubles of the region
-// [x0, x0+w) x [y0, y0+hgt), plus add
+// [x0, x0+w) x [y0, y0+hgt), plus add (not at solid nodes, which export zero)
 template <typename T>
 __global__ void k_export(const Phys<T> P, const T* __restrict__ in, int NP, int k, double* __restrict__ out,
                          double add, int x0, int y0, int w, int hgt) {
   const int xx = blockIdx.x * blockDim.x + threadIdx.x;
   const int yy = blockIdx.y;
   if (xx >= w) return;
+  if (P.obs && ((P.obs[(long long)(y0 + yy) * P.nx + x0 + xx] >> OBS_SOLID) & 1u)) add = 0.0;
   out[(long long)yy * w + xx] = double(in[ix(P, NP, k, x0 + xx, y0 + yy)]) + add;
 }
 
@@ -1720,6 +1776,8 @@ __global__ void k_import(const Phys<T> P, const double* __restrict__ in, T* __re
 
 // Diagnostics, Eqs. (42)-(43), from the MACRO planes and phi(t-1).
 // Per block: [sum phi, sum trS^2, sum S_m^2, max|u|, non-finite, count].
+// Sums and maxima run over the fluid nodes; the averages skip nodes next to
+// a wall or a solid node (a reflecting link).
 constexpr int DIAG_THREADS = 256;
 constexpr int DIAG_FIELDS = 6;
 
@@ -1766,6 +1824,8 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(const Phys<T> P, 
   for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(n / P.nx), x = (int)(n - (long long)y * P.nx);
+    const unsigned om = P.obs ? P.obs[n] : 0u;
+    if ((om >> OBS_SOLID) & 1u) continue;
     const long long id = ix(P, NMACRO, 0, x, y);
     const double phi = double(mac[MAC_PHI * pl + id]);
     const double u = double(mac[MAC_UX * pl + id]), vv = double(mac[MAC_UY * pl + id]);
@@ -1777,6 +1837,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(const Phys<T> P, 
       v[3] = fmax(v[3], sqrt(um2));
     }
     if ((P.wall_x && (x == 0 || x == P.nx - 1)) || (P.wall_y && (y == 0 || y == P.ny - 1))) continue;
+    if (om & 0xffu) continue;
     const double trS = double(mac[MAC_TRS * pl + id]);
     double div = 0.0;
 #pragma unroll

@@ -171,6 +171,50 @@ cudaError_t launch_diag(const Phys<T>& P, const T* macro, const T* phi_prev, dou
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_obs_links(const Phys<T>& P, const unsigned char* solid, uint16_t* obs, cudaStream_t s) {
+  k_obs_links<T><<<row_grid(P.nx, P.ny, OBS_THREADS), OBS_THREADS, 0, s>>>(P, solid, obs);
+  return cudaGetLastError();
+}
+
+template <class C, int MODEL, int MODE, bool UR>
+static cudaError_t obs_passes(const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B,
+                              typename C::value_t* phis, typename C::value_t* mus, cudaStream_t s) {
+  using T = typename C::value_t;
+  const dim3 grid = row_grid(P.nx, P.ny, OBS_THREADS);
+  k_obs_phi<C, MODE == MODE_INIT ? MODE_INIT : MODE_STEP><<<grid, OBS_THREADS, 0, s>>>(P, B, phis);
+  k_obs_fill<T><<<grid, OBS_THREADS, 0, s>>>(P, phis);
+  if (MODEL == MODEL_CH) {
+    k_obs_mu<T><<<grid, OBS_THREADS, 0, s>>>(P, phis, mus);
+    k_obs_fill<T><<<grid, OBS_THREADS, 0, s>>>(P, mus);
+  }
+  k_obs_node<C, MODEL, MODE, UR><<<grid, OBS_THREADS, 0, s>>>(P, B, phis, mus);
+  return cudaGetLastError();
+}
+
+template <class C, int MODEL>
+static cudaError_t obs_model(int mode, const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B,
+                             typename C::value_t* phis, typename C::value_t* mus, bool unit_rates,
+                             cudaStream_t s) {
+  switch (mode) {
+    case MODE_STEP:
+      return unit_rates ? obs_passes<C, MODEL, MODE_STEP, true>(P, B, phis, mus, s)
+                        : obs_passes<C, MODEL, MODE_STEP, false>(P, B, phis, mus, s);
+    case MODE_MACRO: return obs_passes<C, MODEL, MODE_MACRO, false>(P, B, phis, mus, s);
+    case MODE_HIST: return obs_passes<C, MODEL, MODE_HIST, false>(P, B, phis, mus, s);
+    case MODE_INIT: return obs_passes<C, MODEL, MODE_INIT, false>(P, B, phis, mus, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class C>
+cudaError_t launch_obs(int model, int mode, const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B,
+                       typename C::value_t* phis, typename C::value_t* mus, bool unit_rates, cudaStream_t s) {
+  if (!P.obs || !phis || (model == MODEL_CH && !mus)) return cudaErrorInvalidValue;
+  return model == MODEL_CH ? obs_model<C, MODEL_CH>(mode, P, B, phis, mus, unit_rates, s)
+                           : obs_model<C, MODEL_AC>(mode, P, B, phis, mus, unit_rates, s);
+}
+
 // One adjoint step (or, with hist_only, the adjoint of the history set-up at
 // t = 0 without the reverse streaming).  state: snapshot of the step's input
 // state (f* set, g* set of pop_bytes each, then the 5 history planes).
@@ -222,7 +266,9 @@ cudaError_t launch_adjoint_init(const Phys<T>& P, const AdjBufs& A, double* out,
   template cudaError_t launch_step_tma<C>(const Phys<C::value_t>&, const Bufs<C::value_t>&, int*,   \
                                           bool, cudaStream_t);                                      \
   template cudaError_t launch_step_tma_ch<C>(const Phys<C::value_t>&, const Bufs<C::value_t>&, int*, \
-                                             bool, cudaStream_t);
+                                             bool, cudaStream_t);                                   \
+  template cudaError_t launch_obs<C>(int, int, const Phys<C::value_t>&, const Bufs<C::value_t>&,    \
+                                     C::value_t*, C::value_t*, bool, cudaStream_t);
 
 #define PFLBM_INSTANTIATE_DEV(C)                                                                    \
   PFLBM_INSTANTIATE_CODEC(C)                                                                        \
@@ -246,6 +292,7 @@ cudaError_t launch_adjoint_init(const Phys<T>& P, const AdjBufs& A, double* out,
                                               double*, bool, cudaStream_t);                       \
   template cudaError_t launch_adjoint_seed<T>(const Phys<T>&, const double*, const AdjBufs&,      \
                                               cudaStream_t);                                      \
-  template cudaError_t launch_adjoint_init<T>(const Phys<T>&, const AdjBufs&, double*, cudaStream_t);
+  template cudaError_t launch_adjoint_init<T>(const Phys<T>&, const AdjBufs&, double*, cudaStream_t); \
+  template cudaError_t launch_obs_links<T>(const Phys<T>&, const unsigned char*, uint16_t*, cudaStream_t);
 
 }  // namespace pflbm

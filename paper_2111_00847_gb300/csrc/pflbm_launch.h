@@ -10,6 +10,7 @@
 
 #include "pflbm_kernels.cuh"
 #include "pflbm_adjoint.cuh"
+#include "pflbm_obstacle.cuh"
 
 namespace pflbm {
 
@@ -47,6 +48,14 @@ cudaError_t launch_import(const Phys<T>& P, const double* in, T* out, int NP, in
 template <typename T>
 cudaError_t launch_diag(const Phys<T>& P, const T* macro, const T* phi_prev, double* partial,
                         int nparts, double* out, cudaStream_t s);
+// solid obstacles (pflbm_obstacle.cuh): the reflecting links of every node
+// from a dense byte mask, and one step (or MACRO / HIST / INIT pass) through
+// the obstacle passes; phis, mus: one-plane work planes of the arithmetic type
+template <typename T>
+cudaError_t launch_obs_links(const Phys<T>& P, const unsigned char* solid, uint16_t* obs, cudaStream_t s);
+template <class C>
+cudaError_t launch_obs(int model, int mode, const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B,
+                       typename C::value_t* phis, typename C::value_t* mus, bool unit_rates, cudaStream_t s);
 // discrete adjoint of the Allen-Cahn step (pflbm_adjoint.cuh), plain storage
 template <typename T>
 cudaError_t launch_adjoint_step(const Phys<T>& P, const void* state, long long pop_bytes, const AdjBufs& A,
