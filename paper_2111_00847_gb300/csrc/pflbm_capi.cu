@@ -60,6 +60,8 @@ struct lbm_handle {
   // mu_phi work planes of the obstacle passes
   uint16_t* dobs = nullptr;
   void* obs_planes = nullptr;
+  int* dfill = nullptr;  // solid nodes next to fluid (dense indices)
+  int nfill = 0;
 };
 
 static std::string g_create_error;
@@ -242,6 +244,8 @@ static Phys<T> make_phys(const lbm_handle* h) {
   }
   P.dv_c0 = T(h->dv_c0);
   P.obs = h->dobs;
+  P.obs_fill = h->dfill;
+  P.obs_nfill = h->nfill;
   return P;
 }
 
@@ -668,26 +672,55 @@ int lbm_set_solid(lbm_handle* h, const uint8_t* solid) {
   const long long N = (long long)h->nx * h->ny;
   if (solid)
     for (long long n = 0; n < N; ++n) nsolid += solid[n] != 0;
-  if (nsolid == 0) {  // no obstacles: back to the fused kernels
+  if (h->dobs) {  // drop the previous mask's buffers
     if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
     dev_free(h, h->dobs);
     dev_free(h, h->obs_planes);
+    dev_free(h, h->dfill);
     h->dobs = nullptr;
     h->obs_planes = nullptr;
-    return LBM_OK;
+    h->dfill = nullptr;
+    h->nfill = 0;
   }
-  if (!h->dobs) {
-    h->dobs = (uint16_t*)dev_alloc(h, (size_t)N * sizeof(uint16_t));
-    h->obs_planes = dev_alloc(h, 2 * (size_t)h->plane * h->esize);
-    if (!h->dobs || !h->obs_planes) {
-      dev_free(h, h->dobs);
-      dev_free(h, h->obs_planes);
-      h->dobs = nullptr;
-      h->obs_planes = nullptr;
-      return fail(h, LBM_ENOMEM, "obstacle planes");
-    }
-    CUDA_TRY(h, cudaMemsetAsync(h->obs_planes, 0, 2 * (size_t)h->plane * h->esize, h->stream));
+  if (nsolid == 0) return LBM_OK;  // no obstacles: the fused kernels
+  // solid nodes with a fluid node among their 8 neighbours (periodic sides
+  // wrap; nothing lies beyond a wall)
+  std::vector<int> fill;
+  {
+    const int nx = h->nx, ny = h->ny;
+    const bool wx = h->prm.bc[LBM_LEFT] == LBM_WALL, wy = h->prm.bc[LBM_BOTTOM] == LBM_WALL;
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        if (!solid[(long long)y * nx + x]) continue;
+        bool near = false;
+        for (int dy = -1; dy <= 1 && !near; ++dy)
+          for (int dx = -1; dx <= 1 && !near; ++dx) {
+            int xn = x + dx, yn = y + dy;
+            if (xn < 0 || xn >= nx) { if (wx) continue; xn = (xn + nx) % nx; }
+            if (yn < 0 || yn >= ny) { if (wy) continue; yn = (yn + ny) % ny; }
+            near = !solid[(long long)yn * nx + xn];
+          }
+        if (near) fill.push_back(y * nx + x);
+      }
   }
+  h->dobs = (uint16_t*)dev_alloc(h, (size_t)N * sizeof(uint16_t));
+  h->obs_planes = dev_alloc(h, 2 * (size_t)h->plane * h->esize);
+  h->dfill = (int*)dev_alloc(h, std::max<size_t>(fill.size(), 1) * sizeof(int));
+  if (!h->dobs || !h->obs_planes || !h->dfill) {
+    dev_free(h, h->dobs);
+    dev_free(h, h->obs_planes);
+    dev_free(h, h->dfill);
+    h->dobs = nullptr;
+    h->obs_planes = nullptr;
+    h->dfill = nullptr;
+    return fail(h, LBM_ENOMEM, "obstacle planes");
+  }
+  h->nfill = (int)fill.size();
+  CUDA_TRY(h, cudaMemsetAsync(h->obs_planes, 0, 2 * (size_t)h->plane * h->esize, h->stream));
+  if (!fill.empty())
+    CUDA_TRY(h, cudaMemcpyAsync(h->dfill, fill.data(), fill.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                h->stream));
   // the byte mask goes through the staging buffer (N bytes <= N doubles)
   int rc = ensure_stage(h, 1);
   if (rc) return rc;

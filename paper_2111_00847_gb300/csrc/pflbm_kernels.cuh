@@ -94,6 +94,10 @@ struct Phys {
   // bit i-1 (i = 1..8) set when link i reflects, i.e. its upstream node
   // x - c_i is solid or lies beyond a wall; bit OBS_SOLID set at solid nodes.
   const uint16_t* obs;
+  // solid nodes with a fluid node among their 8 neighbours (dense indices
+  // y * nx + x): the only solid nodes a fluid stencil reads
+  const int* obs_fill;
+  int obs_nfill;
 };
 constexpr int OBS_SOLID = 8;
 
@@ -240,35 +244,42 @@ __device__ __forceinline__ void pull9(const void* buf_, const Phys<typename C::v
   }
 }
 
-// The same pull on a grid with solid obstacles: a link flagged in P.obs
-// reflects (half-way bounce-back at the solid surface, as at a wall); the
-// others wrap across periodic sides.  A solid node sees no populations.
+// The same pull on a grid with solid obstacles, given the node's link word
+// m (P.obs): a flagged link reflects (half-way bounce-back at the solid
+// surface, as at a wall); a solid node sees no populations.  The nine
+// streamed loads are issued first, from wrapped (always in-grid) upstream
+// nodes, so that their addresses do not wait for m; the reflected links are
+// then reloaded, which only nodes next to a boundary do.
 template <class C>
 __device__ __forceinline__ void pull9_obs(const void* buf_, const Phys<typename C::value_t>& P, int set, int x,
-                                          int r, typename C::value_t out[9]) {
+                                          int r, unsigned m, typename C::value_t out[9]) {
   using T = typename C::value_t;
-  const unsigned m = P.obs[(long long)r * P.nx + x];
   const unsigned char* buf = static_cast<const unsigned char*>(buf_);
   constexpr int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
   constexpr int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
   constexpr int op[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-  if ((m >> OBS_SOLID) & 1u) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) out[i] = T(0);
-    return;
+  for (int i = 0; i < 9; ++i) {
+    int sx = x - cx[i], sy = r - cy[i];
+    sx = sx < 0 ? sx + P.nx : (sx >= P.nx ? sx - P.nx : sx);
+    sy = sy < 0 ? sy + P.ny : (sy >= P.ny ? sy - P.ny : sy);
+    out[i] = pop_ld<C>(buf, P, set, i, sx, sy);
   }
-  out[0] = pop_ld<C>(buf, P, set, 0, x, r);
+  if (m & 0x1ffu) {
+    if ((m >> OBS_SOLID) & 1u) {
 #pragma unroll
-  for (int i = 1; i < 9; ++i) {
-    if ((m >> (i - 1)) & 1u) {
-      out[i] = pop_ld<C>(buf, P, set, op[i], x, r);
-    } else {
-      int sx = x - cx[i], sy = r - cy[i];
-      sx = sx < 0 ? sx + P.nx : (sx >= P.nx ? sx - P.nx : sx);
-      sy = sy < 0 ? sy + P.ny : (sy >= P.ny ? sy - P.ny : sy);
-      out[i] = pop_ld<C>(buf, P, set, i, sx, sy);
+      for (int i = 0; i < 9; ++i) out[i] = T(0);
+      return;
     }
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+      if ((m >> (i - 1)) & 1u) out[i] = pop_ld<C>(buf, P, set, op[i], x, r);
   }
+}
+template <class C>
+__device__ __forceinline__ void pull9_obs(const void* buf_, const Phys<typename C::value_t>& P, int set, int x,
+                                          int r, typename C::value_t out[9]) {
+  pull9_obs<C>(buf_, P, set, x, r, (unsigned)P.obs[(long long)r * P.nx + x], out);
 }
 
 // Encode and store the nine post-collision populations v of node (x, y)

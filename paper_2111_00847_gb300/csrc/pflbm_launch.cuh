@@ -182,11 +182,12 @@ static cudaError_t obs_passes(const Phys<typename C::value_t>& P, const Bufs<typ
                               typename C::value_t* phis, typename C::value_t* mus, cudaStream_t s) {
   using T = typename C::value_t;
   const dim3 grid = row_grid(P.nx, P.ny, OBS_THREADS);
+  const int fill_blocks = (P.obs_nfill + OBS_THREADS - 1) / OBS_THREADS;
   k_obs_phi<C, MODE == MODE_INIT ? MODE_INIT : MODE_STEP><<<grid, OBS_THREADS, 0, s>>>(P, B, phis);
-  k_obs_fill<T><<<grid, OBS_THREADS, 0, s>>>(P, phis);
+  if (fill_blocks) k_obs_fill<T><<<fill_blocks, OBS_THREADS, 0, s>>>(P, phis);
   if (MODEL == MODEL_CH) {
     k_obs_mu<T><<<grid, OBS_THREADS, 0, s>>>(P, phis, mus);
-    k_obs_fill<T><<<grid, OBS_THREADS, 0, s>>>(P, mus);
+    if (fill_blocks) k_obs_fill<T><<<fill_blocks, OBS_THREADS, 0, s>>>(P, mus);
   }
   k_obs_node<C, MODEL, MODE, UR><<<grid, OBS_THREADS, 0, s>>>(P, B, phis, mus);
   return cudaGetLastError();
