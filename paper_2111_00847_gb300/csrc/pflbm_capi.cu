@@ -302,7 +302,8 @@ static cudaError_t launch_mode(lbm_handle* h, int mode, const Phys<typename C::v
   using T = typename C::value_t;
   if (!h->dobs) return launch_march<C>(h->prm.phase_model, mode, P, B, h->stream);
   T* phis = (T*)h->obs_planes;
-  return launch_obs<C>(h->prm.phase_model, mode, P, B, phis, phis + h->plane, h->unit_rates, h->stream);
+  return launch_obs<C>(h->prm.phase_model, mode, P, B, phis, phis + h->plane, h->unit_rates, h->derr, h->use_tma,
+                       h->stream);
 }
 
 template <class C>

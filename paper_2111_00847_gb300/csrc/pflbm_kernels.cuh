@@ -153,6 +153,7 @@ struct Bufs {
   T* hist;        // 5 interleaved planes
   T* macro;       // NMACRO interleaved planes (MACRO)
   T* phi_prev;    // optional: phi(t) of the stepped time (STEP / HIST)
+  const T* phis;  // solid obstacles: phi with the neutral-wetting fill (one plane)
   const double* iphi;  // INIT inputs, dense [ny][nx]
   const double* iux;
   const double* iuy;
@@ -1017,6 +1018,23 @@ __device__ __forceinline__ void pull_staged(const unsigned char* rm, const unsig
   out[8] = (bxm || byp) ? stg_ld<C, SEG>(r0, 6, c, r2, is) : stg_ld<C, SEG>(rp, 8, c - 1, r2, is);
 }
 
+// The same pull where the reflecting links come from a node's link word m
+// (P.obs: bit i-1 set when link i's upstream node is solid or beyond a wall).
+template <class C, int SEG, typename T = typename C::value_t>
+__device__ __forceinline__ void pull_staged_obs(const unsigned char* rm, const unsigned char* r0,
+                                                const unsigned char* rp, int c, unsigned m, const T* r2, T is,
+                                                T out[9]) {
+  out[0] = stg_ld<C, SEG>(r0, 0, c, r2, is);
+  out[1] = (m & 1u) ? stg_ld<C, SEG>(r0, 3, c, r2, is) : stg_ld<C, SEG>(r0, 1, c - 1, r2, is);
+  out[2] = (m & 2u) ? stg_ld<C, SEG>(r0, 4, c, r2, is) : stg_ld<C, SEG>(rm, 2, c, r2, is);
+  out[3] = (m & 4u) ? stg_ld<C, SEG>(r0, 1, c, r2, is) : stg_ld<C, SEG>(r0, 3, c + 1, r2, is);
+  out[4] = (m & 8u) ? stg_ld<C, SEG>(r0, 2, c, r2, is) : stg_ld<C, SEG>(rp, 4, c, r2, is);
+  out[5] = (m & 16u) ? stg_ld<C, SEG>(r0, 7, c, r2, is) : stg_ld<C, SEG>(rm, 5, c - 1, r2, is);
+  out[6] = (m & 32u) ? stg_ld<C, SEG>(r0, 8, c, r2, is) : stg_ld<C, SEG>(rm, 6, c + 1, r2, is);
+  out[7] = (m & 64u) ? stg_ld<C, SEG>(r0, 5, c, r2, is) : stg_ld<C, SEG>(rp, 7, c + 1, r2, is);
+  out[8] = (m & 128u) ? stg_ld<C, SEG>(r0, 6, c, r2, is) : stg_ld<C, SEG>(rp, 8, c - 1, r2, is);
+}
+
 // Launch shape of the TMA step per storage codec: strip width, rows staged
 // ahead of need (f, g), resident threads per SM it is compiled for
 // (registers), and whether the f pulled for phi of row y+1 is kept in
@@ -1052,7 +1070,12 @@ struct TmaCfg {
 };
 
 // VSEG: segments of P.seg_rows rows (small grids) instead of the constant LY.
-template <class C, bool UR, bool VSEG = false>
+// OBS: solid obstacles (P.obs).  phi, with the neutral-wetting values at
+// solid nodes, comes from the plane B.phis (written by k_obs_phi and
+// k_obs_fill before the launch) instead of from the staged rows; the pulls
+// reflect the links flagged in each node's link word; solid nodes store
+// zeros.  The staging, rings and barriers are those of the plain step.
+template <class C, bool UR, bool VSEG = false, bool OBS = false>
 __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>::TBX)
     k_step_tma(const Phys<typename C::value_t> P, const Bufs<typename C::value_t> B, int* __restrict__ err) {
   using T = typename C::value_t;
@@ -1128,11 +1151,32 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
   // left halo (thread 0), right halo (thread w - 1); x-wall ghosts from the
   // thread's own phi and a second pull of the neighbouring column.
   T fnext[9];  // FK: the pulled f of the last phi row made with keep set
+  unsigned mnext = 0;  // OBS and FK: the link word of that row's node
+  // OBS: phi of row r from the filled plane (x-wall ghosts as in the plain
+  // step, from the plane's columns 0, 1 and nx-1, nx-2)
+  auto phi_row_plane = [&](int r) {
+    const int rr = wrap_row(r);
+    T* dst = sp + tslot(r) * (TBX + 2);
+    if (!active) return;
+    const T* pr = B.phis + ix(P, 1, 0, 0, rr);
+    dst[tid + 1] = pr[x];
+    if (tid == 0) dst[0] = x0 > 0 ? pr[x0 - 1] : (!wx ? pr[nx - 1] : wall_ghost(P, SIDE_LEFT, pr[0], pr[1]));
+    if (tid == w - 1)
+      dst[w + 1] = x0 + w < nx ? pr[x0 + w] : (!wx ? pr[0] : wall_ghost(P, SIDE_RIGHT, pr[nx - 1], pr[nx - 2]));
+  };
   auto phi_row_at = [&](int r, const unsigned char* rm, const unsigned char* r0, const unsigned char* rp,
                         bool keep) {
     const int rr = wrap_row(r);
     const bool bym = wy && rr == 0, byp = wy && rr == ny - 1;
     T* dst = sp + tslot(r) * (TBX + 2);
+    if constexpr (OBS) {
+      phi_row_plane(r);
+      if (FK && keep && active) {
+        mnext = P.obs[(long long)rr * nx + x];
+        pull_staged_obs<C, SEG>(rm, r0, rp, tid + XPAD, mnext, rf2, isf, fnext);
+      }
+      return;
+    }
     if (!active) return;
     T v[9];
     if (edge_x || bym || byp)
@@ -1172,6 +1216,10 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
   // SLIM: phi of row y0 - 1 (in the domain or wrapped) from pulls of the
   // global planes, since its f rows are not staged.
   auto phi_row_global = [&](int r) {
+    if constexpr (OBS) {
+      phi_row_plane(r);
+      return;
+    }
     const int rr = wrap_row(r);
     T* dst = sp + tslot(r) * (TBX + 2);
     if (!active) return;
@@ -1244,9 +1292,11 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
     if (y + 2 <= f_last) ok = mbar_wait_bounded(&barF[fW], fWp) && ok;
     if (y + 1 <= g_last) ok = mbar_wait_bounded(&barG[gW], gWp) && ok;
     T f[9];  // pulled f of row y (FK: made with phi of row y)
+    unsigned mc = 0;  // OBS: link word of the node of row y
     if (FK) {
 #pragma unroll
       for (int i = 0; i < 9; ++i) f[i] = fnext[i];
+      mc = mnext;
     }
     const unsigned char* f_m = sf + add(fR0, RF - 1, RF) * FS;  // f row y-1 (not SLIM)
     const unsigned char* f_0 = sf + fR0 * FS;                   // f row y
@@ -1294,7 +1344,11 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
       const unsigned char* g_p = sg + add(gA, 2, RG) * FS;
       const bool bym = wy && y == 0, byp = wy && y == ny - 1;
       T g[9];
-      if (edge_x || bym || byp) {  // bounce-back links possible (block-uniform test)
+      if constexpr (OBS) {
+        if (!FK) mc = P.obs[(long long)y * nx + x];
+        if (!FK) pull_staged_obs<C, SEG>(f_m, f_0, f_p, tid + XPAD, mc, rf2, isf, f);
+        pull_staged_obs<C, SEG>(g_m, g_0, g_p, tid + XPAD, mc, rg2, isg, g);
+      } else if (edge_x || bym || byp) {  // bounce-back links possible (block-uniform test)
         const bool bxm = wx && x == 0, bxp = wx && x == nx - 1;
         if (!FK) pull_staged<C, SEG>(f_m, f_0, f_p, tid + XPAD, bxm, bxp, bym, byp, rf2, isf, f);
         pull_staged<C, SEG>(g_m, g_0, g_p, tid + XPAD, bxm, bxp, bym, byp, rg2, isg, g);
@@ -1302,7 +1356,18 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
         if (!FK) pull_staged<C, SEG>(f_m, f_0, f_p, tid + XPAD, false, false, false, false, rf2, isf, f);
         pull_staged<C, SEG>(g_m, g_0, g_p, tid + XPAD, false, false, false, false, rg2, isg, g);
       }
-      node_update<C, MODEL_AC, MODE_STEP, UR>(P, B, x, y, phi9, phi9, f, g, h, T(0), T(0), T(0));
+      if (OBS && ((mc >> OBS_SOLID) & 1u)) {  // a solid node: no populations, no history
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = T(0);
+        store_pops<C>(P, B.fout, 0, x, y, f, T(0), true);
+        store_pops<C>(P, B.gout, 1, x, y, f, T(0), false);
+        T* hb = B.hist + ix(P, 5, 0, x, y);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) hb[k * P.pitch] = T(0);
+        if (B.phi_prev) B.phi_prev[ix(P, 1, 0, x, y)] = T(0);
+      } else {
+        node_update<C, MODEL_AC, MODE_STEP, UR>(P, B, x, y, phi9, phi9, f, g, h, T(0), T(0), T(0));
+      }
     }
 #pragma unroll
     for (int k = 0; k < 5; ++k) h[k] = hn[k];

@@ -57,28 +57,29 @@ static int tma_segment_rows(int nx, int ny) {
   return segment_rows(nx, ny, G::TBX, G::threads / G::TBX);
 }
 
-template <class C, bool UR, bool VSEG>
+template <class C, bool UR, bool VSEG, bool OBS = false>
 static cudaError_t launch_tma_seg(const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B,
                                   int* err, cudaStream_t s) {
   using G = TmaCfg<C>;
   using L = TmaLayout<C, G::TBX, G::DF, G::DG, G::slim>;
   // per function and device; cheap next to a step
-  cudaError_t e = cudaFuncSetAttribute(k_step_tma<C, UR, VSEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_step_tma<C, UR, VSEG, OBS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L::bytes);
   if (e != cudaSuccess) return e;
   const dim3 grid((P.nx + G::TBX - 1) / G::TBX, (P.ny + P.seg_rows - 1) / P.seg_rows);
-  k_step_tma<C, UR, VSEG><<<grid, G::TBX, L::bytes, s>>>(P, B, err);
+  k_step_tma<C, UR, VSEG, OBS><<<grid, G::TBX, L::bytes, s>>>(P, B, err);
   return cudaGetLastError();
 }
 
 // Segments of LY rows use the instantiation with the constant length (its
 // register allocation is the tuned one); shorter ones the runtime-length one.
-template <class C, bool UR>
+template <class C, bool UR, bool OBS = false>
 static cudaError_t launch_tma_variant(const Phys<typename C::value_t>& P0, const Bufs<typename C::value_t>& B,
                                       int* err, cudaStream_t s) {
   Phys<typename C::value_t> P = P0;
   P.seg_rows = tma_segment_rows<C>(P.nx, P.ny);
-  return P.seg_rows == LY ? launch_tma_seg<C, UR, false>(P, B, err, s) : launch_tma_seg<C, UR, true>(P, B, err, s);
+  return P.seg_rows == LY ? launch_tma_seg<C, UR, false, OBS>(P, B, err, s)
+                          : launch_tma_seg<C, UR, true, OBS>(P, B, err, s);
 }
 
 // Cahn-Hilliard step: same segment rule, its own launch shape (TmaChCfg).
@@ -208,10 +209,30 @@ static cudaError_t obs_model(int mode, const Phys<typename C::value_t>& P, const
   }
 }
 
+// Allen-Cahn step with obstacles on the TMA kernel: phi and its fill, then
+// k_step_tma<..., OBS> reading phi from the plane.
+template <class C>
+static cudaError_t obs_step_tma(const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B0,
+                                typename C::value_t* phis, int* err, bool unit_rates, cudaStream_t s) {
+  using T = typename C::value_t;
+  const dim3 grid = row_grid(P.nx, P.ny, OBS_THREADS);
+  const int fill_blocks = (P.obs_nfill + OBS_THREADS - 1) / OBS_THREADS;
+  k_obs_phi<C, MODE_STEP><<<grid, OBS_THREADS, 0, s>>>(P, B0, phis);
+  if (fill_blocks) k_obs_fill<T><<<fill_blocks, OBS_THREADS, 0, s>>>(P, phis);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  Bufs<T> B = B0;
+  B.phis = phis;
+  return unit_rates ? launch_tma_variant<C, true, true>(P, B, err, s) : launch_tma_variant<C, false, true>(P, B, err, s);
+}
+
 template <class C>
 cudaError_t launch_obs(int model, int mode, const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B,
-                       typename C::value_t* phis, typename C::value_t* mus, bool unit_rates, cudaStream_t s) {
+                       typename C::value_t* phis, typename C::value_t* mus, bool unit_rates, int* err,
+                       bool use_tma, cudaStream_t s) {
   if (!P.obs || !phis || (model == MODEL_CH && !mus)) return cudaErrorInvalidValue;
+  if (use_tma && model == MODEL_AC && mode == MODE_STEP && P.nx >= 4 * XPAD)
+    return obs_step_tma<C>(P, B, phis, err, unit_rates, s);
   return model == MODEL_CH ? obs_model<C, MODEL_CH>(mode, P, B, phis, mus, unit_rates, s)
                            : obs_model<C, MODEL_AC>(mode, P, B, phis, mus, unit_rates, s);
 }
@@ -269,7 +290,7 @@ cudaError_t launch_adjoint_init(const Phys<T>& P, const AdjBufs& A, double* out,
   template cudaError_t launch_step_tma_ch<C>(const Phys<C::value_t>&, const Bufs<C::value_t>&, int*, \
                                              bool, cudaStream_t);                                   \
   template cudaError_t launch_obs<C>(int, int, const Phys<C::value_t>&, const Bufs<C::value_t>&,    \
-                                     C::value_t*, C::value_t*, bool, cudaStream_t);
+                                     C::value_t*, C::value_t*, bool, int*, bool, cudaStream_t);
 
 #define PFLBM_INSTANTIATE_DEV(C)                                                                    \
   PFLBM_INSTANTIATE_CODEC(C)                                                                        \

@@ -50,12 +50,15 @@ cudaError_t launch_diag(const Phys<T>& P, const T* macro, const T* phi_prev, dou
                         int nparts, double* out, cudaStream_t s);
 // solid obstacles (pflbm_obstacle.cuh): the reflecting links of every node
 // from a dense byte mask, and one step (or MACRO / HIST / INIT pass) through
-// the obstacle passes; phis, mus: one-plane work planes of the arithmetic type
+// the obstacle passes; phis, mus: one-plane work planes of the arithmetic
+// type.  With use_tma the Allen-Cahn step runs its node update on the TMA
+// kernel (err: its time-out flag).
 template <typename T>
 cudaError_t launch_obs_links(const Phys<T>& P, const unsigned char* solid, uint16_t* obs, cudaStream_t s);
 template <class C>
 cudaError_t launch_obs(int model, int mode, const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B,
-                       typename C::value_t* phis, typename C::value_t* mus, bool unit_rates, cudaStream_t s);
+                       typename C::value_t* phis, typename C::value_t* mus, bool unit_rates, int* err,
+                       bool use_tma, cudaStream_t s);
 // discrete adjoint of the Allen-Cahn step (pflbm_adjoint.cuh), plain storage
 template <typename T>
 cudaError_t launch_adjoint_step(const Phys<T>& P, const void* state, long long pop_bytes, const AdjBufs& A,

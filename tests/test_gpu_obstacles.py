@@ -173,6 +173,43 @@ def test_solid_frame_matches_fused_walls(pk, model, walls):
         assert np.abs(fa - fb).max() <= 1e-12 * max(1.0, np.abs(fa).max()), which
 
 
+@pytest.mark.parametrize("prec", [W.PREC_FP64, W.PREC_FP32, W.PREC_FP16_DEV], ids=["fp64", "fp32", "fp16dev"])
+@pytest.mark.parametrize("walls", ["none", "y", "x", "all"])
+@pytest.mark.parametrize("nx,ny", [(300, 150), (16, 70), (257, 129), (129, 200)])
+def test_tma_obstacle_step_matches_passes(pk, prec, walls, nx, ny):
+    """The Allen-Cahn step with obstacles on the TMA kernel (phi from the
+    filled plane, link words in the staged pulls) and on the one-thread-per-node
+    passes (LBM_FLAG_NO_TMA): rounding-level agreement after one step, the
+    parity bar after 20.  129 columns leave a one-column last strip, 200 rows
+    several segments and a ragged one; the obstacles touch strip and segment
+    boundaries and the walls."""
+    case = W.noisy_drop(nx, ny, precision=prec, walls=walls, noise=0.005, u_amp=0.002,
+                        theta=(60, 120, 45, 135), gravity=(W.GRAV_RHO, 1e-6, -1e-5))
+    solid = obstacles(nx, ny)
+    solid[:, min(nx - 1, 128)] |= np.arange(ny) % 7 == 0  # dots on a strip boundary
+    solid[min(ny - 1, 64), :] |= np.arange(nx) % 5 == 0   # and on a segment boundary
+    sims = []
+    for flags in (0, pk.LBM_FLAG_NO_TMA):
+        sim = pk.Simulation(case.params.with_(flags=flags))
+        sim.set_solid(solid)
+        sim.init_fields(case.phi, case.ux, case.uy, case.p)
+        sims.append(sim)
+    # 16-bit storage: the bars of the fused kernels' A/B test, 0.05 u and 0.2 u
+    # on the populations (a rounding difference can move a deviation by one
+    # 16-bit step)
+    lowp = prec == W.PREC_FP16_DEV
+    u = U16[W.PREC_FP16_DEV]
+    tol1 = {W.PREC_FP64: 1e-14, W.PREC_FP32: 1e-6, W.PREC_FP16_DEV: 0.05 * u}[prec]
+    tol20 = {W.PREC_FP64: 1e-12, W.PREC_FP32: 1e-5, W.PREC_FP16_DEV: 0.2 * u}[prec]
+    for steps, tol in ((1, tol1), (19, tol20)):
+        for sim in sims:
+            sim.step(steps)
+        for which in ((pk.LBM_F_POP, pk.LBM_G_POP) if lowp else (pk.LBM_F_POP, pk.LBM_G_POP, pk.LBM_HIST)):
+            a, b = sims[0].fields(which), sims[1].fields(which)
+            d = np.abs(a - b).max() / max(np.abs(b).max(), 1e-30)
+            assert d <= tol, (steps, which, d)
+
+
 def test_obstacles_can_be_removed_and_adjoint_refuses(pk):
     nx, ny = 64, 48
     case = W.noisy_drop(nx, ny, precision=W.PREC_FP64, walls="y")
