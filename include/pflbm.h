@@ -123,6 +123,14 @@ enum {
  *               Cahn-Hilliard; same arithmetic, for A/B comparison);
  *               0 otherwise.  Grids under 16 columns always use the
  *               register-pipelined kernel.
+ *  n_delta      regularisation of the interface normal of Eq. (8),
+ *               n = grad phi / (|grad phi|^4 + delta^4)^(1/4) with
+ *               delta = n_delta (phiA - phiB) / W (the paper's grad phi /
+ *               |grad phi| is undefined where grad phi = 0); 0 selects the
+ *               default 1e-5.  Larger values (e.g. 5e-3) make the step a
+ *               smoother function of phi, which gradients through long
+ *               unstable runs need, at the cost of weaker sharpening in the
+ *               interface tails.  Must be >= 0.
  */
 typedef struct lbm_params {
     int32_t version, nx, ny, precision;
@@ -134,6 +142,7 @@ typedef struct lbm_params {
     double gx, gy, rho0;
     double theta_deg[4];
     double s_f[9], s_g[9];
+    double n_delta;
 } lbm_params;
 
 typedef struct lbm_handle lbm_handle;

@@ -66,6 +66,7 @@ typedef struct {
     double gx, gy, rho0;
     double theta_deg[4];
     double s_f[9], s_g[9];     /* NaN: the default rule of Sec. 4 */
+    double n_delta;            /* regularisation of n in units of dphi / W; 0: 1e-5 */
 } oracle_params;
 
 enum { O_OK = 0, O_EINVAL = -1, O_ENOMEM = -2, O_EUNSTABLE = -4, O_EUNSUPPORTED = -5 };
@@ -403,18 +404,23 @@ static void phase_pass(ostate *st)
         /* AC: lambda = sqrt(2 beta/k)(phiA - phi)(phi - phiB) = 4 (phiA-phi)(phi-phiB)/(W dphi),
          * n = grad phi / |grad phi|, D = grad phi - lambda n  (Eqs. (7)-(8)).
          * n is undefined where grad phi = 0; reading:
-         *   n = grad phi / (|grad phi|^4 + delta_n^4)^(1/4),  delta_n = 5e-3 dphi / W.
+         *   n = grad phi / (|grad phi|^4 + delta_n^4)^(1/4),
+         *   delta_n = n_delta dphi / W,  n_delta = 1e-5 unless the parameter sets it.
          * It is the unit normal to within (delta_n / |grad phi|)^4 / 4 -- 2.5e-5
          * where |grad phi| = 10 delta_n -- and a smooth function of grad phi
-         * everywhere, so the step is differentiable.  Its slope in the bulk,
-         * about 1/delta_n, bounds how strongly a round-off-level gradient --
-         * where an overshoot phi > phiA (or < phiB) makes lambda nonzero -- can
-         * steer the flux: for the anti-diffusive case (lambda > |grad phi|) the
-         * rate is lambda / delta_n.  Measured on a 64 x 256 RTI (Re 1000), a
-         * one-ulp perturbation of phi0 grows in 2000 steps to 7e-15 with this
-         * delta_n, but to 3e-3 with 3e-3 dphi / W and to 7e-3 within 500 steps
-         * with 1e-3 dphi / W; larger values weaken the interface tails
-         * (phi (1 - phi) below ~1e-3), which the layered Poiseuille error feels. */
+         * everywhere.  Where |grad phi| is not far above delta_n (phi (1 - phi)
+         * below about n_delta / 4 in a tanh profile) the sharpening flux is
+         * weakened and the interface tails widen; with viscosity ratio 1000 a
+         * tail of 1e-3 in phi doubles the light phase's viscosity, so the
+         * layered Poiseuille error of Table 2 needs a small n_delta: 0.277 at
+         * n_delta = 5e-3 against 1.03e-2 at 1e-5 (ratio 1000; Table 2:
+         * 8.4e-3).  The slope of n in the bulk, about 1/delta_n, bounds how
+         * strongly a round-off-level gradient -- where an overshoot
+         * phi > phiA (or < phiB) makes lambda nonzero -- can steer the flux
+         * (for lambda > |grad phi| the anti-diffusive rate is lambda/delta_n):
+         * on a 64 x 256 RTI (Re 1000) a one-ulp perturbation of phi0 grows in
+         * 2000 steps to 7e-15 with n_delta = 5e-3 but to 3e-3 with 3e-3, so
+         * gradients through long unstable runs take the larger value. */
 #pragma omp parallel for schedule(static)
         for (long n = 0; n < N; ++n) {
             const double ph = st->phi[n];
@@ -755,6 +761,7 @@ static int validate(const oracle_params *P, char *err)
     if (!(P->phiA > P->phiB)) BAD("phiA must exceed phiB");
     if (!(P->rhoA > 0 && P->rhoB > 0 && P->muA > 0 && P->muB > 0)) BAD("densities and viscosities must be positive");
     if (!(P->width > 0 && P->sigma >= 0 && P->mobility >= 0 && P->eta > 0)) BAD("width, sigma, mobility, eta");
+    if (!(P->n_delta >= 0.0 && P->n_delta < 1.0)) BAD("n_delta outside [0, 1)");
     for (int k = 0; k < 9; ++k) {
         if (!isnan(P->s_f[k]) && !(P->s_f[k] > 0 && P->s_f[k] < 2)) BAD("s_f outside (0,2)");
         if (!isnan(P->s_g[k]) && !(P->s_g[k] > 0 && P->s_g[k] < 2)) BAD("s_g outside (0,2)");
@@ -810,7 +817,7 @@ int oracle_create(const oracle_params *P, ostate **out)
      * and given that value when sigma = 0 switches surface tension off */
     st->lam_coef = P->sigma > 0.0 ? sqrt(2.0 * st->beta / st->kappa) : 4.0 / (P->width * st->dphi);
     st->drho_dphi = (P->rhoA - P->rhoB) / st->dphi;
-    st->n_delta = 5e-3 * st->dphi / P->width;
+    st->n_delta = (P->n_delta > 0.0 ? P->n_delta : 1e-5) * st->dphi / P->width;
     for (int k = 0; k < 9; ++k) { st->sf[k] = P->s_f[k]; st->sg[k] = P->s_g[k]; }
     /* App. C (first matrix): H = (s_g^2 - s_g^0)/(9 s_g^0 s_g^2), K = 1/(3c^2) */
     {

@@ -50,7 +50,7 @@ class LbmParams(C.Structure):
         ("muA", C.c_double), ("muB", C.c_double), ("mobility", C.c_double), ("width", C.c_double),
         ("sigma", C.c_double), ("eta", C.c_double), ("gx", C.c_double), ("gy", C.c_double),
         ("rho0", C.c_double), ("theta_deg", C.c_double * 4), ("s_f", C.c_double * 9),
-        ("s_g", C.c_double * 9),
+        ("s_g", C.c_double * 9), ("n_delta", C.c_double),
     ]
 
 
@@ -125,6 +125,7 @@ def params_struct(prm) -> LbmParams:
     for k in range(9):
         s.s_f[k] = float(prm.s_f[k])
         s.s_g[k] = float(prm.s_g[k])
+    s.n_delta = float(getattr(prm, "n_delta", 0.0))
     return s
 
 

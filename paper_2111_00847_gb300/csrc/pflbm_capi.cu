@@ -138,6 +138,7 @@ static int validate(const lbm_params* P) {
   if (!(P->phiA > P->phiB)) return fail(nullptr, LBM_EINVAL, "phiA must exceed phiB");
   if (!(P->rhoA > 0 && P->rhoB > 0 && P->muA > 0 && P->muB > 0)) return fail(nullptr, LBM_EINVAL, "densities and viscosities must be positive");
   if (!(P->width > 0 && P->sigma >= 0 && P->mobility >= 0 && P->eta > 0)) return fail(nullptr, LBM_EINVAL, "width > 0, sigma >= 0, mobility >= 0, eta > 0 required");
+  if (!(P->n_delta >= 0.0 && P->n_delta < 1.0)) return fail(nullptr, LBM_EINVAL, "n_delta must lie in [0, 1)");
   for (int k = 0; k < 9; ++k) {
     if (!std::isnan(P->s_f[k]) && !(P->s_f[k] > 0 && P->s_f[k] < 2)) return fail(nullptr, LBM_EINVAL, "s_f[%d] outside (0, 2)", k);
     if (!std::isnan(P->s_g[k]) && !(P->s_g[k] > 0 && P->s_g[k] < 2)) return fail(nullptr, LBM_EINVAL, "s_g[%d] outside (0, 2)", k);
@@ -215,7 +216,7 @@ static Phys<T> make_phys(const lbm_handle* h) {
   P.beta4 = T(4.0 * h->beta);
   P.kappa = T(h->kappa);
   P.lam_coef = T(h->lam_coef);
-  P.n_delta = T(5e-3 * (Q.phiA - Q.phiB) / Q.width);
+  P.n_delta = T((Q.n_delta > 0.0 ? Q.n_delta : 1e-5) * (Q.phiA - Q.phiB) / Q.width);
   P.drho = T(h->drho);
   P.rhoB = T(Q.rhoB);
   P.rho_mean = T(0.5 * (Q.rhoA + Q.rhoB));

@@ -50,7 +50,8 @@ def test_params_struct_layout(pk):
     """The ctypes image matches the C layout (int32 block, then doubles)."""
     s = pk.LbmParams
     assert s.phiA.offset == 14 * 4
-    assert C.sizeof(s) == 14 * 4 + 35 * 8
+    assert C.sizeof(s) == 14 * 4 + 36 * 8
+    assert s.n_delta.offset == 14 * 4 + 35 * 8
 
 
 def _bad(prm_kw):
@@ -66,6 +67,7 @@ def _bad(prm_kw):
     (dict(s_f=(1.0, 1.0, 1.0, 2.5, 1, 1, 1, 1, 1)), -1), (dict(width=0.5), -1),
     (dict(precision=7), -1), (dict(flux_model=W.FLUX_CORRECTED), -5),
     (dict(phase_model=7), -1), (dict(nx=70000, ny=70000), -1), (dict(flags=8), -1),
+    (dict(n_delta=-1e-3), -1),
 ])
 def test_create_rejects_bad_parameters(pk, kw, code):
     with pytest.raises(pk.LbmError) as ei:
