@@ -127,10 +127,14 @@ enum {
  *               n = grad phi / (|grad phi|^4 + delta^4)^(1/4) with
  *               delta = n_delta (phiA - phiB) / W (the paper's grad phi /
  *               |grad phi| is undefined where grad phi = 0); 0 selects the
- *               default 1e-5.  Larger values (e.g. 5e-3) make the step a
- *               smoother function of phi, which gradients through long
- *               unstable runs need, at the cost of weaker sharpening in the
- *               interface tails.  Must be >= 0.
+ *               default 5e-3, which keeps the step a smooth, well-conditioned
+ *               function of phi (round-off-level gradients in the bulk cannot
+ *               steer the sharpening flux; gradients through long unstable
+ *               runs exist).  It weakens the sharpening in the far interface
+ *               tails, phi (1 - phi) below about n_delta / 4, which flows with
+ *               a large viscosity ratio feel (the layered channel of Sec. 4.2
+ *               needs 1e-5); small values make rounding differences grow
+ *               quickly on rough or unstable flows.  Must lie in [0, 1).
  */
 typedef struct lbm_params {
     int32_t version, nx, ny, precision;

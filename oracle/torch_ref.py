@@ -69,7 +69,7 @@ class TorchScheme:
                          else 4.0 / (prm.width * dphi))                   # Eq. (8)
         self.drho = (prm.rhoA - prm.rhoB) / dphi                          # Eq. (10)
         nd = getattr(prm, "n_delta", 0.0)
-        self.delta_n = (nd if nd > 0 else 1e-5) * dphi / prm.width
+        self.delta_n = (nd if nd > 0 else 5e-3) * dphi / prm.width
         sfm = 1.0 / (prm.mobility / (prm.eta * CS2) + 0.5)
         self.Sf = [(sfm if k in (3, 5) else 1.0) if math.isnan(prm.s_f[k]) else prm.s_f[k] for k in range(9)]
         self.Sg = [1.0 if math.isnan(prm.s_g[k]) else prm.s_g[k] for k in range(9)]

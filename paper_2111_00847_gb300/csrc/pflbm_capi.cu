@@ -216,7 +216,7 @@ static Phys<T> make_phys(const lbm_handle* h) {
   P.beta4 = T(4.0 * h->beta);
   P.kappa = T(h->kappa);
   P.lam_coef = T(h->lam_coef);
-  P.n_delta = T((Q.n_delta > 0.0 ? Q.n_delta : 1e-5) * (Q.phiA - Q.phiB) / Q.width);
+  P.n_delta = T((Q.n_delta > 0.0 ? Q.n_delta : 5e-3) * (Q.phiA - Q.phiB) / Q.width);
   P.drho = T(h->drho);
   P.rhoB = T(Q.rhoB);
   P.rho_mean = T(0.5 * (Q.rhoA + Q.rhoB));

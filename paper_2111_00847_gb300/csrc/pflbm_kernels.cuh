@@ -397,7 +397,7 @@ __device__ __forceinline__ void node_update(const Phys<T>& P, const Bufs<T>& B, 
     // chemical potential, Eq. (5)
     mu = P.beta4 * (phi - P.phiA) * (phi - P.phiB) * (phi - P.phibar) - P.kappa * lap;
     // conservative AC flux, Eqs. (7)-(8), n = grad phi / (|grad phi|^4 + delta_n^4)^(1/4)
-    // (delta_n = n_delta dphi / W, default n_delta 1e-5: the unit normal across
+    // (delta_n = n_delta dphi / W, default n_delta 5e-3: the unit normal across
     // the interface, and a smooth function of grad phi with slope about
     // 1/delta_n in the bulk, where |grad phi| -> 0)
     lam = P.lam_coef * (P.phiA - phi) * (phi - P.phiB);
