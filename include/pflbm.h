@@ -259,6 +259,17 @@ int lbm_set_fields(lbm_handle *h, int32_t which, const double *in);
  */
 int lbm_set_solid(lbm_handle *h, const uint8_t *solid);
 
+/*
+ * Self-test of the failure path (no counterpart in the paper).  Launches on
+ * the handle's stream one wait, with the step kernels' bounded wait, on a
+ * barrier that nothing arrives on; after about 4 ms it gives up and raises
+ * the handle's device flag, as a step kernel does when its staged rows
+ * never land.  The next call that synchronises (lbm_fields, diagnostics)
+ * returns LBM_ECUDA with that message and clears the flag; the handle and
+ * its state stay usable.  Returns LBM_OK once launched.
+ */
+int lbm_selftest_wait_timeout(lbm_handle *h);
+
 /* Number of time steps taken since lbm_init_fields. */
 int64_t lbm_time(const lbm_handle *h);
 

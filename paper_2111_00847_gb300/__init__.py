@@ -32,7 +32,7 @@ LBM_FLAG_NO_TMA = 1
 DIAG_KEYS = ("t", "sum_phi", "Du_rms", "Sm_rms", "umax", "nonfinite", "n_avg", "reserved")
 
 EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_fields", "lbm_fields_region",
-            "lbm_fields_noalloc", "lbm_set_fields", "lbm_set_solid",
+            "lbm_fields_noalloc", "lbm_set_fields", "lbm_set_solid", "lbm_selftest_wait_timeout",
             "lbm_time", "lbm_device_bytes", "lbm_destroy", "lbm_last_error",
             "lbm_state_bytes", "lbm_snapshot", "lbm_restore", "lbm_adjoint_seed", "lbm_adjoint_step",
             "lbm_adjoint_init", "lbm_adjoint_gravity")
@@ -87,6 +87,7 @@ def load(path: str | None = None):
     L.lbm_set_fields.argtypes = [C.c_void_p, C.c_int32, dp]
     L.lbm_fields_noalloc.argtypes = [C.c_void_p, C.c_int32, dp]
     L.lbm_set_solid.argtypes = [C.c_void_p, C.POINTER(C.c_uint8)]
+    L.lbm_selftest_wait_timeout.argtypes = [C.c_void_p]
     L.lbm_time.argtypes = [C.c_void_p]
     L.lbm_time.restype = C.c_int64
     L.lbm_device_bytes.argtypes = [C.c_void_p]
@@ -188,6 +189,12 @@ def lbm_set_solid(h, solid: np.ndarray | None):
     """Solid obstacle nodes: [ny][nx] uint8 (nonzero = solid), or None."""
     ptr = None if solid is None else solid.ctypes.data_as(C.POINTER(C.c_uint8))
     _check(load().lbm_set_solid(h, ptr), h)
+
+
+def lbm_selftest_wait_timeout(h):
+    """Make one bounded device wait give up (the failure path of the step
+    kernels); the next synchronising call reports LBM_ECUDA."""
+    _check(load().lbm_selftest_wait_timeout(h), h)
 
 
 def lbm_time(h) -> int:

@@ -738,6 +738,30 @@ int lbm_set_solid(lbm_handle* h, const uint8_t* solid) {
   return LBM_OK;
 }
 
+}  // extern "C"
+
+// One thread waits, with the step kernels' bounded wait, on an mbarrier that
+// nothing arrives on; when the wait gives up it raises the flag exactly as a
+// step kernel whose staged rows never landed does.
+__global__ void k_wait_selftest(int* __restrict__ err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, limit)) atomicOr(err, 1);
+}
+
+extern "C" {
+
+int lbm_selftest_wait_timeout(lbm_handle* h) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  k_wait_selftest<<<1, 32, 0, h->stream>>>(h->derr, 1LL << 12);
+  CUDA_TRY(h, cudaGetLastError());
+  return LBM_OK;
+}
+
 int64_t lbm_time(const lbm_handle* h) { return h ? h->t : -1; }
 
 int64_t lbm_device_bytes(const lbm_handle* h) { return h ? h->bytes : 0; }
