@@ -154,6 +154,7 @@ struct Bufs {
   T* macro;       // NMACRO interleaved planes (MACRO)
   T* phi_prev;    // optional: phi(t) of the stepped time (STEP / HIST)
   const T* phis;  // solid obstacles: phi with the neutral-wetting fill (one plane)
+  const T* mus;   // solid obstacles, Cahn-Hilliard: mu_phi with the fill (one plane)
   const double* iphi;  // INIT inputs, dense [ny][nx]
   const double* iux;
   const double* iuy;
@@ -1433,7 +1434,11 @@ struct TmaChLayout {
   static_assert(P0 % 16 == 0 && PI % 16 == 0, "bulk-copy segments must be 16-byte multiples");
 };
 
-template <class C, bool UR, bool VSEG = false>
+// OBS: solid obstacles (P.obs).  The phi and mu_phi rows come from the
+// filled planes B.phis and B.mus (k_obs_phi, k_obs_mu and k_obs_fill run
+// before the launch), with the same wall ghosts and mirrors; the pulls
+// reflect the links flagged in each node's link word; solid nodes store zeros.
+template <class C, bool UR, bool VSEG = false, bool OBS = false>
 __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaChCfg<C>::TBX)
     k_step_tma_ch(const Phys<typename C::value_t> P, const Bufs<typename C::value_t> B, int* __restrict__ err) {
   using T = typename C::value_t;
@@ -1500,7 +1505,39 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
   // thread 0 columns -1 and -2, thread w-1 columns w and w+1; at an x wall the
   // ghost column from the wetting rule (the column beyond it is not needed:
   // mu_phi is mirrored there).
+  // OBS: phi of row r from the filled plane, the halo columns as above
+  auto phi_row_plane = [&](int r) {
+    const int rr = wrap_row(r);
+    T* dst = prow(r);
+    if (!active) return;
+    const T* pr = B.phis + ix(P, 1, 0, 0, rr);
+    dst[tid + 2] = pr[x];
+    if (tid == 0) {
+      if (x0 > 0 || !wx) {
+        dst[1] = pr[x0 > 0 ? x0 - 1 : nx - 1];
+        dst[0] = pr[x0 > 1 ? x0 - 2 : x0 - 2 + nx];
+      } else {
+        dst[1] = wall_ghost(P, SIDE_LEFT, pr[0], pr[1]);
+        dst[0] = T(0);
+      }
+    }
+    if (tid == w - 1) {
+      if (x0 + w < nx || !wx) {
+        const int a = x0 + w < nx ? x0 + w : x0 + w - nx;
+        const int b = x0 + w + 1 < nx ? x0 + w + 1 : x0 + w + 1 - nx;
+        dst[w + 2] = pr[a];
+        dst[w + 3] = (wx && x0 + w + 1 == nx) ? wall_ghost(P, SIDE_RIGHT, pr[nx - 1], pr[nx - 2]) : pr[b];
+      } else {
+        dst[w + 2] = wall_ghost(P, SIDE_RIGHT, pr[nx - 1], pr[nx - 2]);
+        dst[w + 3] = T(0);
+      }
+    }
+  };
   auto phi_row_at = [&](int r, const unsigned char* rm, const unsigned char* r0, const unsigned char* rp) {
+    if constexpr (OBS) {
+      phi_row_plane(r);
+      return;
+    }
     const int rr = wrap_row(r);
     const bool bym = wy && rr == 0, byp = wy && rr == ny - 1;
     T* dst = prow(r);
@@ -1545,6 +1582,10 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
   };
   // the same from pulls of the global planes (segment starts)
   auto phi_row_global = [&](int r) {
+    if constexpr (OBS) {
+      phi_row_plane(r);
+      return;
+    }
     const int rr = wrap_row(r);
     T* dst = prow(r);
     if (!active) return;
@@ -1595,6 +1636,13 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
     const T* pp = prow(r + 1);
     T* d = mrow(r);
     if (!active) return;
+    if constexpr (OBS) {  // from the filled plane, mirrored at x walls
+      const T* mr = B.mus + ix(P, 1, 0, 0, wrap_row(r));
+      d[tid + 1] = mr[x];
+      if (tid == 0) d[0] = (wx && x0 == 0) ? mr[0] : mr[x0 > 0 ? x0 - 1 : nx - 1];
+      if (tid == w - 1) d[w + 1] = (wx && x0 + w == nx) ? mr[nx - 1] : mr[x0 + w < nx ? x0 + w : 0];
+      return;
+    }
     const T mo = mu_at(pm, p0, pp, tid + 2);
     d[tid + 1] = mo;
     if (tid == 0) d[0] = (wx && x0 == 0) ? mo : mu_at(pm, p0, pp, 1);
@@ -1698,7 +1746,12 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
       mu9[8] = mm[cm + 1];
       const bool bym = wy && y == 0, byp = wy && y == ny - 1;
       T f[9], g[9];
-      if (edge_x || bym || byp) {
+      unsigned mc = 0;
+      if constexpr (OBS) {
+        mc = P.obs[(long long)y * nx + x];
+        pull_staged_obs<C, SEG>(fslot(y - 1), fslot(y), fslot(y + 1), tid + XPAD, mc, rf2, isf, f);
+        pull_staged_obs<C, SEG>(gslot(y - 1), gslot(y), gslot(y + 1), tid + XPAD, mc, rg2, isg, g);
+      } else if (edge_x || bym || byp) {
         const bool bxm = wx && x == 0, bxp = wx && x == nx - 1;
         pull_staged<C, SEG>(fslot(y - 1), fslot(y), fslot(y + 1), tid + XPAD, bxm, bxp, bym, byp, rf2, isf, f);
         pull_staged<C, SEG>(gslot(y - 1), gslot(y), gslot(y + 1), tid + XPAD, bxm, bxp, bym, byp, rg2, isg, g);
@@ -1708,7 +1761,18 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
         pull_staged<C, SEG>(gslot(y - 1), gslot(y), gslot(y + 1), tid + XPAD, false, false, false, false, rg2,
                             isg, g);
       }
-      node_update<C, MODEL_CH, MODE_STEP, UR>(P, B, x, y, phi9, mu9, f, g, h, T(0), T(0), T(0));
+      if (OBS && ((mc >> OBS_SOLID) & 1u)) {  // a solid node: no populations, no history
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = T(0);
+        store_pops<C>(P, B.fout, 0, x, y, f, T(0), true);
+        store_pops<C>(P, B.gout, 1, x, y, f, T(0), false);
+        T* hb = B.hist + ix(P, 5, 0, x, y);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) hb[k * P.pitch] = T(0);
+        if (B.phi_prev) B.phi_prev[ix(P, 1, 0, x, y)] = T(0);
+      } else {
+        node_update<C, MODEL_CH, MODE_STEP, UR>(P, B, x, y, phi9, mu9, f, g, h, T(0), T(0), T(0));
+      }
     }
 #pragma unroll
     for (int k = 0; k < 5; ++k) h[k] = hn[k];

@@ -89,16 +89,16 @@ static int tma_ch_segment_rows(int nx, int ny) {
   return segment_rows(nx, ny, G::TBX, G::threads / G::TBX);
 }
 
-template <class C, bool UR, bool VSEG>
+template <class C, bool UR, bool VSEG, bool OBS = false>
 static cudaError_t launch_tma_ch_seg(const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B,
                                      int* err, cudaStream_t s) {
   using G = TmaChCfg<C>;
   using L = TmaChLayout<C, G::TBX, G::DF, G::DG>;
-  cudaError_t e = cudaFuncSetAttribute(k_step_tma_ch<C, UR, VSEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)L::bytes);
+  cudaError_t e = cudaFuncSetAttribute(k_step_tma_ch<C, UR, VSEG, OBS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (e != cudaSuccess) return e;
   const dim3 grid((P.nx + G::TBX - 1) / G::TBX, (P.ny + P.seg_rows - 1) / P.seg_rows);
-  k_step_tma_ch<C, UR, VSEG><<<grid, G::TBX, L::bytes, s>>>(P, B, err);
+  k_step_tma_ch<C, UR, VSEG, OBS><<<grid, G::TBX, L::bytes, s>>>(P, B, err);
   return cudaGetLastError();
 }
 
@@ -226,6 +226,33 @@ static cudaError_t obs_step_tma(const Phys<typename C::value_t>& P, const Bufs<t
   return unit_rates ? launch_tma_variant<C, true, true>(P, B, err, s) : launch_tma_variant<C, false, true>(P, B, err, s);
 }
 
+// Cahn-Hilliard step with obstacles on the TMA kernel: phi, mu_phi and their
+// fills, then k_step_tma_ch<..., OBS> reading both from the planes.
+template <class C>
+static cudaError_t obs_step_tma_ch(const Phys<typename C::value_t>& P0, const Bufs<typename C::value_t>& B0,
+                                   typename C::value_t* phis, typename C::value_t* mus, int* err, bool unit_rates,
+                                   cudaStream_t s) {
+  using T = typename C::value_t;
+  const dim3 grid = row_grid(P0.nx, P0.ny, OBS_THREADS);
+  const int fill_blocks = (P0.obs_nfill + OBS_THREADS - 1) / OBS_THREADS;
+  k_obs_phi<C, MODE_STEP><<<grid, OBS_THREADS, 0, s>>>(P0, B0, phis);
+  if (fill_blocks) k_obs_fill<T><<<fill_blocks, OBS_THREADS, 0, s>>>(P0, phis);
+  k_obs_mu<T><<<grid, OBS_THREADS, 0, s>>>(P0, phis, mus);
+  if (fill_blocks) k_obs_fill<T><<<fill_blocks, OBS_THREADS, 0, s>>>(P0, mus);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  Bufs<T> B = B0;
+  B.phis = phis;
+  B.mus = mus;
+  Phys<T> P = P0;
+  P.seg_rows = tma_ch_segment_rows<C>(P.nx, P.ny);
+  if (P.seg_rows == LY)
+    return unit_rates ? launch_tma_ch_seg<C, true, false, true>(P, B, err, s)
+                      : launch_tma_ch_seg<C, false, false, true>(P, B, err, s);
+  return unit_rates ? launch_tma_ch_seg<C, true, true, true>(P, B, err, s)
+                    : launch_tma_ch_seg<C, false, true, true>(P, B, err, s);
+}
+
 template <class C>
 cudaError_t launch_obs(int model, int mode, const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B,
                        typename C::value_t* phis, typename C::value_t* mus, bool unit_rates, int* err,
@@ -233,6 +260,8 @@ cudaError_t launch_obs(int model, int mode, const Phys<typename C::value_t>& P, 
   if (!P.obs || !phis || (model == MODEL_CH && !mus)) return cudaErrorInvalidValue;
   if (use_tma && model == MODEL_AC && mode == MODE_STEP && P.nx >= 4 * XPAD)
     return obs_step_tma<C>(P, B, phis, err, unit_rates, s);
+  if (use_tma && model == MODEL_CH && mode == MODE_STEP && P.nx >= 4 * XPAD)
+    return obs_step_tma_ch<C>(P, B, phis, mus, err, unit_rates, s);
   return model == MODEL_CH ? obs_model<C, MODEL_CH>(mode, P, B, phis, mus, unit_rates, s)
                            : obs_model<C, MODEL_AC>(mode, P, B, phis, mus, unit_rates, s);
 }

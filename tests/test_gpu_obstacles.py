@@ -173,17 +173,18 @@ def test_solid_frame_matches_fused_walls(pk, model, walls):
         assert np.abs(fa - fb).max() <= 1e-12 * max(1.0, np.abs(fa).max()), which
 
 
+@pytest.mark.parametrize("model", [W.MODEL_AC, W.MODEL_CH], ids=["ac", "ch"])
 @pytest.mark.parametrize("prec", [W.PREC_FP64, W.PREC_FP32, W.PREC_FP16_DEV], ids=["fp64", "fp32", "fp16dev"])
 @pytest.mark.parametrize("walls", ["none", "y", "x", "all"])
 @pytest.mark.parametrize("nx,ny", [(300, 150), (16, 70), (257, 129), (129, 200)])
-def test_tma_obstacle_step_matches_passes(pk, prec, walls, nx, ny):
-    """The Allen-Cahn step with obstacles on the TMA kernel (phi from the
-    filled plane, link words in the staged pulls) and on the one-thread-per-node
-    passes (LBM_FLAG_NO_TMA): rounding-level agreement after one step, the
-    parity bar after 20.  129 columns leave a one-column last strip, 200 rows
+def test_tma_obstacle_step_matches_passes(pk, prec, walls, nx, ny, model):
+    """The step with obstacles on the TMA kernels (phi, and mu_phi for
+    Cahn-Hilliard, from the filled planes; link words in the staged pulls)
+    and on the one-thread-per-node passes (LBM_FLAG_NO_TMA): rounding-level
+    agreement after one step, the parity bar after 20.  129 columns leave a one-column last strip, 200 rows
     several segments and a ragged one; the obstacles touch strip and segment
     boundaries and the walls."""
-    case = W.noisy_drop(nx, ny, precision=prec, walls=walls, noise=0.005, u_amp=0.002,
+    case = W.noisy_drop(nx, ny, precision=prec, walls=walls, noise=0.005, u_amp=0.002, model=model,
                         theta=(60, 120, 45, 135), gravity=(W.GRAV_RHO, 1e-6, -1e-5))
     solid = obstacles(nx, ny)
     solid[:, min(nx - 1, 128)] |= np.arange(ny) % 7 == 0  # dots on a strip boundary
