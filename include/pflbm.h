@@ -251,11 +251,14 @@ int lbm_set_fields(lbm_handle *h, int32_t which, const double *in);
  * diagnostics sum over fluid nodes and average over fluid nodes without a
  * reflecting link.
  * Takes effect from the next call; call it before lbm_init_fields so that
- * the initial state holds no populations at solid nodes.  With obstacles the
- * step runs as four passes over the grid (five for Cahn-Hilliard) instead of
- * the fused kernels.  Device memory: a 2-byte link word per node and two
- * work planes of the arithmetic type.  The adjoint entry points return
- * LBM_EUNSUPPORTED while obstacles are set.
+ * the initial state holds no populations at solid nodes.  With obstacles a
+ * step first forms phi (Cahn-Hilliard: and mu_phi) on a whole plane and
+ * fills it at the solid nodes next to fluid, then runs the TMA step kernel
+ * reading those planes (3 launches a step; 5 for Cahn-Hilliard; with
+ * LBM_FLAG_NO_TMA or under 16 columns a one-thread-per-node update instead).
+ * Device memory: a 2-byte link word per node, two work planes of the
+ * arithmetic type and the list of solid nodes next to fluid.  The adjoint
+ * entry points return LBM_EUNSUPPORTED while obstacles are set.
  */
 int lbm_set_solid(lbm_handle *h, const uint8_t *solid);
 
