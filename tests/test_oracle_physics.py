@@ -215,17 +215,29 @@ def contact_angle(phi):
     return H, L, math.degrees(2 * math.atan(2 * H / L))
 
 
+# Drop radius, grid and steps per angle: the 30 degree drop spreads to a chord
+# of 67 nodes and takes longer to settle; at 150 degrees the chord is short,
+# and half a node of error in L moves theta by about 2.5 degrees at R0 = 16,
+# so the drop is twice as large.
+CONTACT_CASES = {30.0: (16, 160, 48, 30000), 45.0: (16, 96, 48, 12000), 60.0: (16, 96, 48, 12000),
+                 90.0: (16, 96, 48, 12000), 120.0: (16, 96, 48, 12000), 150.0: (32, 128, 96, 20000)}
+
+
 @pytest.mark.slow
-@pytest.mark.parametrize("theta", [60.0, 120.0])
+@pytest.mark.parametrize("theta", sorted(CONTACT_CASES))
 def test_contact_angle(oracle_mod, theta):
+    """Every angle of Table 3: the angle from theta = 2 arctan(2H/L) within
+    1.5 degrees (or twice the paper's own deviation), and H, L within 5 % of
+    the circular-cap values of Eq. (52)."""
     table = {float(r[0]): float(r[1]) for r in _golden("table3_contact_angle.txt")}
     paper_dev = abs(table[theta] - theta)
-    c = W.droplet_spreading(nx=96, ny=48, R0=16, theta=theta, rhoA=10, muA=1.0, muB=0.1,
+    R0, nx, ny, steps = CONTACT_CASES[theta]
+    c = W.droplet_spreading(nx=nx, ny=ny, R0=R0, theta=theta, rhoA=10, muA=1.0, muB=0.1,
                             W=4.0, mobility=0.1, sigma=0.05, precision=W.PREC_FP64)
-    o = _run(oracle_mod, c, 12000)
+    o = _run(oracle_mod, c, steps)
     H, L, th = contact_angle(o.fields(oracle_mod.PHI))
     assert abs(th - theta) <= max(1.5, 2 * paper_dev), (th, H, L)
-    He, Le, _ = W.spreading_exact(16, theta)
+    He, Le, _ = W.spreading_exact(R0, theta)
     assert abs(H - He) < 0.05 * He and abs(L - Le) < 0.05 * Le
 
 
