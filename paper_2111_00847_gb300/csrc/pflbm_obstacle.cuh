@@ -12,16 +12,19 @@
 // node is zero.
 //
 // The fill needs phi (and, for Cahn-Hilliard, mu_phi) of fluid nodes two
-// (three) nodes away, so the step runs as separate passes over the grid,
-// each one thread per node:
+// (three) nodes away, so these fields are first formed on whole planes, one
+// thread per node:
 //   k_obs_phi   phi = sum_i f_i at fluid nodes (Eq. (22a)) -> phi plane
-//   k_obs_fill  neutral-wetting values at solid nodes (same plane)
+//   k_obs_fill  neutral-wetting values at the solid nodes next to fluid
 //   k_obs_mu    (CH) mu_phi of Eq. (5) at fluid nodes -> mu plane, then
 //               k_obs_fill on it
-//   k_obs_node  the node update of the fused kernels (node_update): stencils
-//               from the planes with the wall ghosts of Eq. (50) (mirror for
-//               mu_phi), pulls with reflection at solid links, collisions,
-//               stores.
+// The step's node update then runs on the TMA step kernels instantiated with
+// OBS (pflbm_kernels.cuh), which read these planes.  k_obs_node is the same
+// update one thread per node: the initial state, history and macroscopic
+// passes, and the step under LBM_FLAG_NO_TMA or on grids under 16 columns.
+// It takes the stencils from the planes with the wall ghosts of Eq. (50)
+// (mirror for mu_phi), pulls with reflection at solid links, collides and
+// stores.
 #pragma once
 
 #include "pflbm_kernels.cuh"
