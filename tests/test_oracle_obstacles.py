@@ -151,11 +151,12 @@ def test_mirror_symmetric_problem_stays_symmetric(oracle_mod, model):
 
 
 def test_fill_is_exact_on_linear_fields(oracle_mod):
-    """The padded phi seen by the stencils at the first macro pass of
-    lbm_init_fields: an isolated solid node inside a linear field shows the
-    field's own value (mean of opposite neighbours), and a solid node whose
-    fluid neighbours are diagonal only (a corner of a solid block) shows their
-    mean."""
+    """The padded phi seen by the stencils after lbm_init_fields: an isolated
+    solid node inside a linear field shows the field's own value (the mean of
+    opposite neighbours); on a 3 x 3 solid block an edge node shows its one
+    fluid axis neighbour, a corner node the mean of its two, and the enclosed
+    centre 0.  (A solid node with diagonal fluid neighbours only occurs at the
+    corners of the solid frame in test_solid_frame_reproduces_neutral_walls.)"""
     nx, ny = 16, 12
     case = W.noisy_drop(nx, ny, walls="none")
     X, Y = np.meshgrid(np.arange(nx) + 0.5, np.arange(ny) + 0.5)
@@ -178,3 +179,25 @@ def test_fill_is_exact_on_linear_fields(oracle_mod):
     assert pad[2 + 1, 9 + 1] == pytest.approx(0.5 * (phi[2, 8] + phi[1, 9]), rel=1e-15)
     # block centre (3, 10): no fluid neighbour at all -> 0
     assert pad[3 + 1, 10 + 1] == 0.0
+
+
+def test_dam_break_obstacle_geometry():
+    """The trapezoid of the last dam break (reading of Sec. 4.5's figure): on
+    the bottom wall, centred at Lx/2, a/2 tall, a/2 wide at the top and 3a/2
+    at the bottom (45-degree flanks), a = Lx/4; the water column a x a at the
+    left, clear of it."""
+    nx, ny = 400, 200
+    case = W.dam_break_obstacle(nx=nx, ny=ny)
+    a = nx // 4
+    s = case.solid
+    rows = np.nonzero(s.any(axis=1))[0]
+    assert rows.min() == 0 and rows.max() == a // 2 - 1
+    for j in (0, a // 4, a // 2 - 1):
+        cols = np.nonzero(s[j])[0]
+        y = j + 0.5
+        half = 0.25 * a + (0.5 * a - y)  # top half-width a/4, slope 1
+        assert cols.min() == int(np.ceil(0.5 * nx - half - 0.5))
+        assert cols.max() == int(np.floor(0.5 * nx + half - 0.5))
+        assert abs((cols.min() + cols.max() + 1) / 2 - 0.5 * nx) < 1e-9  # centred
+    assert not (s & (case.phi > 0.5)).any()
+    assert case.phi[: a - 8, : a - 8].min() > 0.99  # column interior is water
