@@ -242,12 +242,14 @@ def test_contact_angle(oracle_mod, theta):
 
 
 @pytest.mark.slow
-def test_laplace_law(oracle_mod):
+@pytest.mark.parametrize("model", [W.MODEL_AC, W.MODEL_CH], ids=["ac", "ch"])
+def test_laplace_law(oracle_mod, model):
     """p_in - p_out = sigma / R for a 2-D drop (surface force mu grad phi with
-    beta, k of Eq. (3)); W = 4 resolves it to better than 10 %."""
+    beta, k of Eq. (3)), with either phase field; W = 4 resolves it to better
+    than 10 % (Cahn-Hilliard measured 0.992 and 0.984 at R = 12, 16)."""
     res = []
     for R in (12.0, 16.0):
-        c = W.static_drop(64, R, rho_ratio=10.0)
+        c = W.static_drop(64, R, rho_ratio=10.0, model=model)
         o = _run(oracle_mod, c, 8000)
         p = o.fields(oracle_mod.P)
         dp = p[30:34, 30:34].mean() - p[:3, :3].mean()
