@@ -74,39 +74,69 @@ def build(force: bool = False) -> str:
         return _LIB
 
 
+def build_variant(edits, outdir: str, tag: str = "variant"):
+    """Compile a copy of the oracle with textual edits and load it.
+
+    For the tests of the pins themselves: each edit (old, new) plants one
+    mistake (a flipped sign, a wrong coefficient), and a pin must fail on the
+    planted copy.  Every `old` must occur exactly once in the source.  The
+    copy is built in `outdir`; the oracle's own library is not touched."""
+    with open(_SRC) as fh:
+        src = fh.read()
+    for old, new in edits:
+        n = src.count(old)
+        if n != 1:
+            raise ValueError(f"edit target found {n} times: {old!r}")
+        src = src.replace(old, new)
+    os.makedirs(outdir, exist_ok=True)
+    csrc = os.path.join(outdir, f"pflbm_oracle_{tag}.c")
+    so = os.path.join(outdir, f"liboracle_pflbm_{tag}.so")
+    with open(csrc, "w") as fh:
+        fh.write(src)
+    cmd = ["gcc", "-std=c99", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fPIC", "-shared", "-fopenmp",
+           csrc, "-o", so, "-lm"]
+    subprocess.run(cmd, check=True)
+    return _load(so)
+
+
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = C.CDLL(_LIB)
-        dp = C.POINTER(C.c_double)
-        L.oracle_create.argtypes = [C.POINTER(OracleParams), C.POINTER(C.c_void_p)]
-        L.oracle_init_fields.argtypes = [C.c_void_p, dp, dp, dp, dp]
-        L.oracle_step.argtypes = [C.c_void_p, C.c_int64]
-        L.oracle_fields.argtypes = [C.c_void_p, C.c_int32, dp]
-        L.oracle_set_fields.argtypes = [C.c_void_p, C.c_int32, dp]
-        L.oracle_set_solid.argtypes = [C.c_void_p, C.POINTER(C.c_uint8)]
-        L.oracle_padded.argtypes = [C.c_void_p, C.c_int32, dp]
-        L.oracle_destroy.argtypes = [C.c_void_p]
-        L.oracle_destroy.restype = None
-        L.oracle_last_error.argtypes = [C.c_void_p]
-        L.oracle_last_error.restype = C.c_char_p
-        L.oracle_time.argtypes = [C.c_void_p]
-        L.oracle_time.restype = C.c_long
-        L.oracle_set_threads.argtypes = [C.c_int]
-        L.oracle_set_threads.restype = None
-        L.oracle_get_threads.restype = C.c_int
-        L.oracle_moment_matrix.argtypes = [dp, dp]
-        L.oracle_moment_matrix.restype = None
-        L.oracle_lattice.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
-        L.oracle_lattice.restype = None
-        L.oracle_node_moments.argtypes = [C.POINTER(OracleParams), dp, dp]
-        L.oracle_grad_lap.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp]
-        L.oracle_wall_phi.argtypes = [C.POINTER(OracleParams), C.c_double, C.c_double,
-                                      C.c_double, dp]
-        L.oracle_wall_phi.restype = C.c_double
-        _lib = L
+        _lib = _load(_LIB)
     return _lib
+
+
+def _load(path: str):
+    """Load an oracle shared object and declare its entry points."""
+    L = C.CDLL(path)
+    dp = C.POINTER(C.c_double)
+    L.oracle_create.argtypes = [C.POINTER(OracleParams), C.POINTER(C.c_void_p)]
+    L.oracle_init_fields.argtypes = [C.c_void_p, dp, dp, dp, dp]
+    L.oracle_step.argtypes = [C.c_void_p, C.c_int64]
+    L.oracle_fields.argtypes = [C.c_void_p, C.c_int32, dp]
+    L.oracle_set_fields.argtypes = [C.c_void_p, C.c_int32, dp]
+    L.oracle_set_solid.argtypes = [C.c_void_p, C.POINTER(C.c_uint8)]
+    L.oracle_padded.argtypes = [C.c_void_p, C.c_int32, dp]
+    L.oracle_destroy.argtypes = [C.c_void_p]
+    L.oracle_destroy.restype = None
+    L.oracle_last_error.argtypes = [C.c_void_p]
+    L.oracle_last_error.restype = C.c_char_p
+    L.oracle_time.argtypes = [C.c_void_p]
+    L.oracle_time.restype = C.c_long
+    L.oracle_set_threads.argtypes = [C.c_int]
+    L.oracle_set_threads.restype = None
+    L.oracle_get_threads.restype = C.c_int
+    L.oracle_moment_matrix.argtypes = [dp, dp]
+    L.oracle_moment_matrix.restype = None
+    L.oracle_lattice.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
+    L.oracle_lattice.restype = None
+    L.oracle_node_moments.argtypes = [C.POINTER(OracleParams), dp, dp]
+    L.oracle_grad_lap.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp]
+    L.oracle_wall_phi.argtypes = [C.POINTER(OracleParams), C.c_double, C.c_double,
+                                  C.c_double, dp]
+    L.oracle_wall_phi.restype = C.c_double
+    return L
 
 
 def _dptr(a: np.ndarray | None):
@@ -133,11 +163,12 @@ def get_threads() -> int:
 class Oracle:
     """One FP64 CPU simulation (naive whole-grid passes)."""
 
-    def __init__(self, params):
+    def __init__(self, params, lib_=None):
         self.params = params
+        self._L = lib_ if lib_ is not None else lib()
         self._p = to_struct(params)
         h = C.c_void_p()
-        rc = lib().oracle_create(C.byref(self._p), C.byref(h))
+        rc = self._L.oracle_create(C.byref(self._p), C.byref(h))
         if rc != 0:
             raise OracleError(rc, "oracle_create failed (see stderr)")
         self._h = h
@@ -145,14 +176,14 @@ class Oracle:
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().oracle_destroy(self._h)
+            self._L.oracle_destroy(self._h)
             self._h = None
 
     __del__ = close
 
     def _check(self, rc):
         if rc != 0:
-            raise OracleError(rc, lib().oracle_last_error(self._h).decode())
+            raise OracleError(rc, self._L.oracle_last_error(self._h).decode())
 
     def _arr(self, a):
         if a is None:
@@ -165,24 +196,24 @@ class Oracle:
         """Solid nodes: mask [ny][nx], nonzero = solid (None removes them)."""
         if mask is None:
             self._solid = None
-            self._check(lib().oracle_set_solid(self._h, None))
+            self._check(self._L.oracle_set_solid(self._h, None))
             return
         m = np.ascontiguousarray(np.asarray(mask) != 0, dtype=np.uint8)
         assert m.shape == (self.ny, self.nx), m.shape
         self._solid = m
-        self._check(lib().oracle_set_solid(self._h, m.ctypes.data_as(C.POINTER(C.c_uint8))))
+        self._check(self._L.oracle_set_solid(self._h, m.ctypes.data_as(C.POINTER(C.c_uint8))))
 
     def init_fields(self, phi, ux=None, uy=None, p=None):
         arrs = [self._arr(x) for x in (phi, ux, uy, p)]
         self._keep = arrs
-        self._check(lib().oracle_init_fields(self._h, *[_dptr(a) for a in arrs]))
+        self._check(self._L.oracle_init_fields(self._h, *[_dptr(a) for a in arrs]))
 
     def step(self, n: int = 1):
-        self._check(lib().oracle_step(self._h, int(n)))
+        self._check(self._L.oracle_step(self._h, int(n)))
 
     @property
     def t(self) -> int:
-        return int(lib().oracle_time(self._h))
+        return int(self._L.oracle_time(self._h))
 
     def fields(self, which: int) -> np.ndarray:
         N = self.nx * self.ny
@@ -195,19 +226,19 @@ class Oracle:
         else:
             out = np.empty((self.ny, self.nx))
         del N
-        self._check(lib().oracle_fields(self._h, int(which), _dptr(out)))
+        self._check(self._L.oracle_fields(self._h, int(which), _dptr(out)))
         return out
 
     def padded(self, which: int = 0) -> np.ndarray:
         """[ny+2][nx+2] phi (which 0) or mu_phi (1) as the last macro pass's
         stencils saw them (ghost layer included)."""
         out = np.empty((self.ny + 2, self.nx + 2))
-        self._check(lib().oracle_padded(self._h, int(which), _dptr(out)))
+        self._check(self._L.oracle_padded(self._h, int(which), _dptr(out)))
         return out
 
     def set_fields(self, which: int, arr: np.ndarray):
         a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64))
-        self._check(lib().oracle_set_fields(self._h, int(which), _dptr(a)))
+        self._check(self._L.oracle_set_fields(self._h, int(which), _dptr(a)))
 
     def diag(self) -> dict:
         d = self.fields(DIAG)
