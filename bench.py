@@ -36,6 +36,8 @@ import workloads as W  # noqa: E402
 METRIC = "fused-step MLUPS (phase+flow) and % HBM roofline; adjoint/forward time ratio"
 UNIT = "MLUPS"
 FALLBACK_HBM_GBS = 6800.0
+# GB300's FP64 rate (non-tensor), nominal: the FP64 step is bound by it
+FP64_NOMINAL_GFLOPS = 1250.0
 PRECISIONS = {  # name: (lbm precision, dtype label, algorithmic bytes per lattice update)
     "fp32": (W.PREC_FP32, "f32", 46 * 4),
     "fp64": (W.PREC_FP64, "f64", 46 * 8),
@@ -101,10 +103,11 @@ def measured_peak():
     return FALLBACK_HBM_GBS, "of fallback"
 
 
-def profiled_traffic(precision):
+def profiled_traffic(precision, key=None):
     """DRAM bytes per lattice update of the step kernel, from the committed
-    ncu summary (profiles/*.txt line 'dram_bytes_per_lu_<precision>: X')."""
-    key = f"dram_bytes_per_lu_{precision}"
+    ncu summary (profiles/*.txt line 'dram_bytes_per_lu_<precision>: X');
+    `key` reads another per-update figure the same way."""
+    key = key or f"dram_bytes_per_lu_{precision}"
     for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.txt"))):
         for line in open(f):
             m = re.match(rf"\s*{key}\s*:\s*([0-9.eE+-]+)", line)
@@ -391,10 +394,12 @@ def main():
         return
     case = W.rti_multimode(n, precision=prec)
 
-    def timed_steps(params, label, per_lu_bytes, phi0=None):
+    def timed_steps(params, label, per_lu_bytes, phi0=None, steps=None):
         """W warm-up steps, then K steps timed with CUDA events on the
         simulation's stream (barrier + synchronize on both sides); the
         roofline of the fused step kernel (one launch per step)."""
+        nodes = params.nx * params.ny
+        nsteps = args.steps if steps is None else steps
         s = pk.Simulation(params, stream=stream)
         s.init_fields(case.phi if phi0 is None else phi0)
         s.step(args.warmup)
@@ -406,17 +411,17 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        s.step(args.steps)
+        s.step(nsteps)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
         ck = clk_s.stop()
         t_ms = max_over_ranks(e0.elapsed_time(e1))
-        launch_s = t_ms / 1e3 / args.steps
-        ach = per_lu_bytes * N / launch_s / 1e9
+        launch_s = t_ms / 1e3 / nsteps
+        ach = per_lu_bytes * nodes / launch_s / 1e9
         tr, tr_from = profiled_traffic(label)
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": (tr * N if tr is not None else None), "peak_source": peak_src,
+                "traffic": (tr * nodes if tr is not None else None), "peak_source": peak_src,
                 "algorithmic_bytes_per_lu": per_lu_bytes, "traffic_source": tr_from}
         return s, t_ms, roof, ck
 
@@ -487,6 +492,26 @@ def main():
         del sch
         models = {"cahn_hilliard": {"value": whole_job_mlups(world, N, args.steps, msch / 1e3), "unit": UNIT,
                                     "ms_per_step": msch / args.steps, "roofline": roofch, "clocks": clkch}}
+        # the FP64 step (the path held to 1e-12 against the oracle): RTI
+        # 8192^2, K/5 steps; bound by GB300's FP64 pipe, not by HBM
+        n64 = 8192
+        c64 = W.rti_multimode(n64, precision=W.PREC_FP64)
+        k64 = max(1, args.steps // 5)
+        s64, ms64, roof64, clk64 = timed_steps(c64.params, "fp64", PRECISIONS["fp64"][2], c64.phi, steps=k64)
+        s64.close()
+        del s64
+        lups64 = n64 * n64 * k64 / (ms64 / 1e3)
+        fl, fl_from = profiled_traffic("fp64", key="fp64_flops_per_lu")
+        alu = None
+        if fl is not None:
+            ach = fl * lups64 / 1e9
+            alu = {"bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+                   "frac": ach / FP64_NOMINAL_GFLOPS, "traffic": None,
+                   "peak_source": "nominal FP64 rate of GB300 (no measured FP64 peak)",
+                   "flops_per_lu": fl, "flops_source": fl_from}
+        models["fp64"] = {"value": whole_job_mlups(world, n64 * n64, k64, ms64 / 1e3), "unit": UNIT,
+                          "workload": workload_name(n64), "steps": k64, "ms_per_step": ms64 / k64,
+                          "roofline": alu, "hbm_frac": roof64["frac"], "clocks": clk64}
 
     # ---- the same workload with 16-bit deviation storage (FP32 arithmetic)
     storage = None

@@ -219,12 +219,15 @@ int lbm_fields_region(lbm_handle *h, int32_t which, int32_t x0, int32_t y0, int3
  * Same result as lbm_fields for LBM_F_POP, LBM_G_POP or LBM_HIST, but with
  * no device allocation at any point (the paper has no counterpart: this is
  * a service of the library).  For callers that cannot let the library
- * allocate: code recording a CUDA stream capture, applications that
- * reserve all device memory up front, callers whose device is full.
+ * allocate: applications that reserve all device memory up front, callers
+ * whose device is full.
  * Planes are staged in one fixed 8 MiB array inside the library
  * (1,048,576 doubles), so grids above 1,048,576 nodes get LBM_EINVAL, as
- * do other selectors.  The first call on each device looks up that array's
- * address; make it before any stream capture starts.  The array is shared
+ * do other selectors.  The handle's device (the one current at lbm_create)
+ * must be current: otherwise LBM_EINVAL.  The first call on each device
+ * looks up that array's address; make it before any stream capture starts.
+ * The looked-up addresses are kept in an atomic per-device cache, so first
+ * calls from several host threads at once are safe.  The array is shared
  * by all calls and keeps the last call's contents; calls that run on the GPU
  * at the same time race on it.  Synchronises the handle's stream.
  */

@@ -5,6 +5,7 @@
 // and the sequencing of launches on the handle's stream.  Every step of the
 // method runs in the device kernels of pflbm_kernels.cuh.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -24,6 +25,7 @@ struct lbm_handle {
   lbm_allocator alloc{};
   bool have_alloc = false;
   int prec = LBM_FP64;
+  int device = -1;       // the CUDA device current at lbm_create (all of the handle's memory is there)
   size_t esize = 8;      // bytes of the arithmetic type (history, macro planes)
   long long pop_bytes = 0;  // bytes of one population set (codec layout)
   int nx = 0, ny = 0, pitch = 0;
@@ -589,6 +591,11 @@ int lbm_create(const lbm_params* params, void* stream, const lbm_allocator* allo
   if (!h) return fail(nullptr, LBM_ENOMEM, "host allocation");
   h->prm = *params;
   h->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(nullptr, LBM_ECUDA, "cannot query the current CUDA device");
+  }
   if (alloc) {
     h->alloc = *alloc;
     h->have_alloc = true;
@@ -783,18 +790,20 @@ const char* lbm_last_error(const lbm_handle* h) { return h ? h->err.c_str() : g_
 //
 // lbm_fields stages each exported plane in a device buffer that the handle
 // creates on first use.  Some callers cannot let the library allocate at
-// that point: code that is recording a CUDA stream capture (cudaMalloc is
-// not permitted there), applications that reserve all device memory up
-// front and forbid later allocations, and callers running with the device
-// already full.  lbm_fields_noalloc exports the same planes through a
-// fixed staging array compiled into the library instead.
+// that point: applications that reserve all device memory up front and
+// forbid later allocations, and callers running with the device already
+// full.  lbm_fields_noalloc exports the same planes through a fixed staging
+// array compiled into the library instead.
 //
 // The array is a file-scope __device__ variable of NOALLOC_MAX_NODES
 // doubles (8 MiB).  Every GPU that loads the library holds it until the
 // process exits.  Host code cannot use the array's name as a device
 // address, so the first call on each device looks the address up with
-// cudaGetSymbolAddress while that device is current.  That first call
-// should therefore come before any stream capture begins.
+// cudaGetSymbolAddress while that device is current (the handle's device:
+// a call made while another device is current is refused).  That first call
+// should come before any stream capture begins.  The per-device address
+// cache is atomic: host threads that make their first calls at the same
+// time each look up the same address and store it, which is harmless.
 //
 // All calls share the one array, and it keeps whatever the last call left
 // in it.  The export overwrites every element it later reads, so nothing
@@ -804,18 +813,23 @@ const char* lbm_last_error(const lbm_handle* h) { return h ? h->err.c_str() : g_
 static constexpr long long NOALLOC_MAX_NODES = 1LL << 20;
 static constexpr int NOALLOC_MAX_DEVICES = 64;
 static __device__ __align__(256) double g_noalloc_stage[NOALLOC_MAX_NODES];
-static double* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};  // device address per device ordinal
+static std::atomic<double*> g_noalloc_addr[NOALLOC_MAX_DEVICES];  // device address per device ordinal
 
 static int noalloc_stage_for_device(lbm_handle* h, double** out) {
   int dev = -1;
   CUDA_TRY(h, cudaGetDevice(&dev));
+  if (dev != h->device)
+    return fail(h, LBM_EINVAL, "lbm_fields_noalloc: device %d is current, but the handle lives on device %d", dev,
+                h->device);
   if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(h, LBM_EINVAL, "device %d out of range", dev);
-  if (!g_noalloc_addr[dev]) {
+  double* a = g_noalloc_addr[dev].load(std::memory_order_acquire);
+  if (!a) {
     void* p = nullptr;
     CUDA_TRY(h, cudaGetSymbolAddress(&p, g_noalloc_stage));
-    g_noalloc_addr[dev] = static_cast<double*>(p);
+    a = static_cast<double*>(p);
+    g_noalloc_addr[dev].store(a, std::memory_order_release);
   }
-  *out = g_noalloc_addr[dev];
+  *out = a;
   return LBM_OK;
 }
 

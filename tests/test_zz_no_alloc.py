@@ -1,7 +1,7 @@
 """lbm_fields_noalloc: the population / history export that allocates no
-device memory, for callers that cannot let the library allocate (inside a
-CUDA stream capture, with all device memory reserved up front, or with the
-device full).  Its output must equal what lbm_fields returns.
+device memory, for callers that cannot let the library allocate (with all
+device memory reserved up front, or with the device full).  Its output must
+equal what lbm_fields returns.
 
 This file is collected last on purpose, and every test in it works both in
 a fresh process and after the rest of the suite."""
@@ -66,3 +66,24 @@ def test_noalloc_rejects_large_grids_and_other_fields(pk):
     rc, _ = _noalloc(pk, sim, pk.LBM_PHI, (48, 64))
     assert rc == pk.LBM_EINVAL
     sim.close()
+
+
+def test_noalloc_refuses_a_call_from_another_device(pk):
+    """The staging array's address is per device; a call made while a device
+    other than the handle's is current is refused, not run against the other
+    device's array."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs a second CUDA device")
+    small = W.noisy_drop(64, 48, precision=W.PREC_FP32)
+    with torch.cuda.device(0):
+        sim = pk.Simulation(small.params)
+        sim.init_fields(small.phi)
+    with torch.cuda.device(1):
+        rc, _ = _noalloc(pk, sim, pk.LBM_F_POP, (9, 48, 64))
+    assert rc == pk.LBM_EINVAL
+    assert "handle lives on device" in pk.lbm_last_error(sim.handle)
+    with torch.cuda.device(0):
+        rc, _ = _noalloc(pk, sim, pk.LBM_F_POP, (9, 48, 64))
+        assert rc == pk.LBM_OK
+        sim.close()

@@ -482,3 +482,63 @@ def flat_interface(nx: int, ny: int, model: int = MODEL_AC, W: float = 4.0,
                  mobility=0.05, width=W, sigma=0.01)
     _, Y = _coords(nx, ny)
     return Case("flat_interface", prm, tanh_profile(Y - 0.5 * ny, W, phiA, phiB))
+
+
+# --------------------------------------------------------------------------
+# The paper's six workloads at sizes the oracle runs in seconds, several
+# strips and segments of the step kernels wide with ragged tails (the parity
+# cases of the CUDA path and of the oracle's sensitivity record).
+# --------------------------------------------------------------------------
+PAPER_PARITY_CASES = ("square_droplet_ac", "square_droplet_ch", "rti", "droplet_spreading", "dam_break",
+                      "layered_poiseuille")
+
+
+def paper_parity_case(name: str, precision: int = PREC_FP64, n_delta: float | None = None) -> Case:
+    """One of PAPER_PARITY_CASES; n_delta (None: the case's own value)
+    sets the regularisation of the interface normal."""
+    if name == "square_droplet_ac":
+        c = square_droplet(n=256, D=128, precision=precision)
+    elif name == "square_droplet_ch":
+        c = square_droplet(n=260, D=128, precision=precision)
+        c.params.phase_model = MODEL_CH
+        c.params.phiA, c.params.phiB = 1.0, -1.0
+        c.phi = 2.0 * c.phi - 1.0
+    elif name == "rti":
+        c = rti(260, 300, d=260.0, amp0=26.0, precision=precision)
+    elif name == "droplet_spreading":
+        c = droplet_spreading(nx=300, ny=150, R0=60.0, theta=60.0, precision=precision)
+    elif name == "dam_break":
+        # the less viscous air of the first dam-break recipe (nu_B = 0.1,
+        # nu_A = 0.01): the harder case for the normal's conditioning
+        c = dam_break(nx=300, ny=150, col_w=100, col_h=100, nuB=0.1, precision=precision)
+    elif name == "layered_poiseuille":
+        c = layered_poiseuille(nx=4, ny=256, precision=precision)
+    else:
+        raise ValueError(name)
+    c.name = name
+    if n_delta is not None:
+        c.params = c.params.with_(n_delta=n_delta)
+    return c
+
+
+# Rough seeded inputs that exercise every boundary, model, gravity mode,
+# viscosity law, flux model and rate path (noise on phi, u and p excites
+# grid-scale dynamics), 300 x 150.
+STRESS_CASES = {
+    "periodic_ac": dict(walls="none"),
+    "ywalls_wet_ac": dict(walls="y", theta=(90, 90, 50, 130), gravity=(GRAV_RHO_MINUS_MEAN, 0.0, -2e-5)),
+    "xwalls_wet_ac": dict(walls="x", theta=(40, 140, 90, 90), gravity=(GRAV_RHO, 1e-5, 0.0)),
+    "allwalls_ac_inverse_nu": dict(walls="all", theta=(60, 120, 75, 105), gravity=(GRAV_RHO, 0.0, -1e-5),
+                                   visc_law=VISC_INVERSE_NU),
+    "periodic_ch": dict(walls="none", model=MODEL_CH),
+    "allwalls_ch": dict(walls="all", model=MODEL_CH, theta=(70, 110, 80, 100), gravity=(GRAV_CONST, 1e-6, -1e-6)),
+    "original_flux": dict(walls="y", flux=FLUX_ORIGINAL),
+    "mrt_rates": dict(walls="none", s_f=(1.0, 1.2, 0.8, 0.9, 1.1, 0.9, 1.3, 1.0, 1.0),
+                      s_g=(1.0, 1.1, 0.9, 1.0, 1.7, 1.0, 1.7, NAN, NAN)),
+}
+
+
+def stress_case(name: str, precision: int = PREC_FP64) -> Case:
+    c = noisy_drop(300, 150, precision=precision, noise=0.005, u_amp=0.002, **STRESS_CASES[name])
+    c.name = name
+    return c
