@@ -82,6 +82,8 @@ enum { LBM_PERIODIC = 0, LBM_WALL = 1 };
 enum { LBM_LEFT = 0, LBM_RIGHT = 1, LBM_BOTTOM = 2, LBM_TOP = 3 };
 /* lbm_params.flags */
 enum { LBM_FLAG_NO_TMA = 1 };
+/* ghost rows on each exchanging side of a y-slab (lbm_create_slab) */
+enum { LBM_SLAB_GHOST = 4 };
 /* lbm_fields / lbm_set_fields selector */
 enum {
     LBM_PHI = 0,   /* order parameter phi = sum_i f_i          [ny][nx]    */
@@ -323,6 +325,51 @@ int lbm_adjoint_seed(lbm_handle *h, const double *dJ_dphi);
 int lbm_adjoint_step(lbm_handle *h, const void *state);
 int lbm_adjoint_init(lbm_handle *h, const void *state0, double *dJ_dphi0);
 int lbm_adjoint_gravity(lbm_handle *h, double *dJ_dG);
+
+/*
+ * y-slab decomposition: one grid divided into bands of rows, one handle per
+ * band (on one device or on several), with a halo exchange between steps.
+ * The paper calls its scheme fully parallel (Introduction): a node's update
+ * reads only its neighbours (the streaming of Eqs. (17) and (40), the
+ * stencils of Eqs. (C.9)-(C.10)), so a band advances exactly as the same
+ * rows of the undivided grid once its neighbours' boundary rows are known.
+ *
+ * lbm_create_slab: a handle over the global rows [y_lo, y_lo + ny_own) of
+ *   the grid `global` describes (ny_own >= LBM_SLAB_GHOST, and less than
+ *   the whole grid).  Locally it holds ghost_lo + ny_own + ghost_hi rows:
+ *   LBM_SLAB_GHOST ghost rows on each side that borders another slab (with
+ *   periodic y, both sides), none on a side that is a global wall.  Every
+ *   other call works on the local rows: lbm_init_fields, lbm_set_fields and
+ *   lbm_fields take and give [local rows][nx] arrays (pass the global
+ *   initial fields of rows y_lo - ghost_lo ... y_lo + ny_own + ghost_hi - 1,
+ *   wrapped in a periodic y).  lbm_step advances one step per call
+ *   (LBM_EINVAL for more): after each step, and after lbm_init_fields or
+ *   lbm_set_fields, exchange the halos before the next step.  The
+ *   diagnostics (lbm_fields LBM_DIAG, taken after the exchange; at
+ *   diag_every the step records phi(t-1) for S_m but computes nothing)
+ *   cover the own rows; slabs combine exactly by summing the
+ *   sums and weighting the rms values with their n_avg.  Solid obstacles and
+ *   the adjoint: LBM_EUNSUPPORTED.
+ * lbm_slab_info: info = {y_lo, ny_own, ghost_lo, ghost_hi} ({0, ny, 0, 0}
+ *   for an undivided handle).
+ * lbm_slab_halo_bytes: bytes of one side's halo message (negative: error).
+ * lbm_slab_pack: copy the message of `side` (LBM_BOTTOM or LBM_TOP) into
+ *   dst, device memory of at least lbm_slab_halo_bytes bytes: the
+ *   LBM_SLAB_GHOST own rows next to that side of the f set, then of the g
+ *   set (post-collision populations, the library's storage layout).
+ * lbm_slab_unpack: write the neighbour's message (its pack of the facing
+ *   side: the upper neighbour's LBM_BOTTOM message into this slab's
+ *   LBM_TOP side) into the ghost rows of `side`.
+ *   Both are asynchronous copies on the handle's stream; order the
+ *   transport (a peer copy, NCCL) after the pack and before the unpack.  A
+ *   side that is a global wall: LBM_EINVAL.
+ */
+int lbm_create_slab(const lbm_params *global, int32_t y_lo, int32_t ny_own, void *cuda_stream,
+                    const lbm_allocator *alloc, lbm_handle **out);
+int lbm_slab_info(const lbm_handle *h, int32_t info[4]);
+int64_t lbm_slab_halo_bytes(const lbm_handle *h);
+int lbm_slab_pack(lbm_handle *h, int32_t side, void *dst);
+int lbm_slab_unpack(lbm_handle *h, int32_t side, const void *src);
 
 #ifdef __cplusplus
 }

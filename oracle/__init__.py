@@ -274,32 +274,32 @@ NODE_KEYS = ("phi", "mu", "u", "v", "p", "rho", "mcx", "mcy", "Fx", "Fy", "drx",
              "lam", "nx", "ny", "dphiu", "dphiv", "dum", "dA", "dB")
 
 
-def node_moments(params, **vals):
+def node_moments(params, lib_=None, **vals):
     """Moment vectors (m_f^eq, m_R, m_g^eq, m_F) the oracle uses at one node."""
     inp = np.array([float(vals.get(k, 0.0)) for k in NODE_KEYS])
     out = np.empty(36)
     s = to_struct(params)
-    rc = lib().oracle_node_moments(C.byref(s), _dptr(inp), _dptr(out))
+    rc = (lib_ or lib()).oracle_node_moments(C.byref(s), _dptr(inp), _dptr(out))
     if rc != 0:
         raise OracleError(rc, "node_moments")
     return out[0:9], out[9:18], out[18:27], out[27:36]
 
 
-def grad_lap(field: np.ndarray):
+def grad_lap(field: np.ndarray, lib_=None):
     f = np.ascontiguousarray(field, dtype=np.float64)
     ny, nx = f.shape
     gx, gy, lp = np.empty_like(f), np.empty_like(f), np.empty_like(f)
-    rc = lib().oracle_grad_lap(nx, ny, _dptr(f), _dptr(gx), _dptr(gy), _dptr(lp))
+    rc = (lib_ or lib()).oracle_grad_lap(nx, ny, _dptr(f), _dptr(gx), _dptr(gy), _dptr(lp))
     if rc != 0:
         raise OracleError(rc, "grad_lap")
     return gx, gy, lp
 
 
-def wall_phi(params, phi1: float, phi2: float, theta_deg: float):
+def wall_phi(params, phi1: float, phi2: float, theta_deg: float, lib_=None):
     """(phi_w, ghost) of the wetting boundary for the given first/second fluid values."""
     s = to_struct(params)
     ghost = np.zeros(1)
-    pw = lib().oracle_wall_phi(C.byref(s), float(phi1), float(phi2), float(theta_deg), _dptr(ghost))
+    pw = (lib_ or lib()).oracle_wall_phi(C.byref(s), float(phi1), float(phi2), float(theta_deg), _dptr(ghost))
     return float(pw), float(ghost[0])
 
 

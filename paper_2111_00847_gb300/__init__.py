@@ -29,13 +29,16 @@ LBM_FP64, LBM_FP32, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2, 3
 LBM_NDIAG = 8
 LBM_ABI_VERSION = 1
 LBM_FLAG_NO_TMA = 1
+LBM_LEFT, LBM_RIGHT, LBM_BOTTOM, LBM_TOP = 0, 1, 2, 3
+LBM_SLAB_GHOST = 4
 DIAG_KEYS = ("t", "sum_phi", "Du_rms", "Sm_rms", "umax", "nonfinite", "n_avg", "reserved")
 
 EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_fields", "lbm_fields_region",
             "lbm_fields_noalloc", "lbm_set_fields", "lbm_set_solid", "lbm_selftest_wait_timeout",
             "lbm_time", "lbm_device_bytes", "lbm_destroy", "lbm_last_error",
             "lbm_state_bytes", "lbm_snapshot", "lbm_restore", "lbm_adjoint_seed", "lbm_adjoint_step",
-            "lbm_adjoint_init", "lbm_adjoint_gravity")
+            "lbm_adjoint_init", "lbm_adjoint_gravity", "lbm_create_slab", "lbm_slab_info",
+            "lbm_slab_halo_bytes", "lbm_slab_pack", "lbm_slab_unpack")
 
 
 class LbmParams(C.Structure):
@@ -104,6 +107,14 @@ def load(path: str | None = None):
     L.lbm_adjoint_step.argtypes = [C.c_void_p, C.c_void_p]
     L.lbm_adjoint_init.argtypes = [C.c_void_p, C.c_void_p, dp]
     L.lbm_adjoint_gravity.argtypes = [C.c_void_p, dp]
+    L.lbm_create_slab.argtypes = [C.POINTER(LbmParams), C.c_int32, C.c_int32, C.c_void_p,
+                                  C.POINTER(LbmAllocator), C.POINTER(C.c_void_p)]
+    L.lbm_create_slab.restype = C.c_int
+    L.lbm_slab_info.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
+    L.lbm_slab_halo_bytes.argtypes = [C.c_void_p]
+    L.lbm_slab_halo_bytes.restype = C.c_int64
+    L.lbm_slab_pack.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
+    L.lbm_slab_unpack.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
     _lib = L
     return L
 
@@ -238,6 +249,36 @@ def lbm_adjoint_gravity(h, out: np.ndarray):
     _check(load().lbm_adjoint_gravity(h, _dptr(out)), h)
 
 
+def lbm_create_slab(params: LbmParams, y_lo: int, ny_own: int, stream: int = 0,
+                    allocator: LbmAllocator | None = None):
+    h = C.c_void_p()
+    rc = load().lbm_create_slab(C.byref(params), int(y_lo), int(ny_own), C.c_void_p(stream or None),
+                                C.byref(allocator) if allocator is not None else None, C.byref(h))
+    _check(rc)
+    return h
+
+
+def lbm_slab_info(h):
+    info = (C.c_int32 * 4)()
+    _check(load().lbm_slab_info(h, info), h)
+    return tuple(int(v) for v in info)
+
+
+def lbm_slab_halo_bytes(h) -> int:
+    n = int(load().lbm_slab_halo_bytes(h))
+    if n < 0:
+        _check(n, h)
+    return n
+
+
+def lbm_slab_pack(h, side: int, dst_ptr: int):
+    _check(load().lbm_slab_pack(h, int(side), C.c_void_p(int(dst_ptr))), h)
+
+
+def lbm_slab_unpack(h, side: int, src_ptr: int):
+    _check(load().lbm_slab_unpack(h, int(side), C.c_void_p(int(src_ptr))), h)
+
+
 # ---- PyTorch plumbing --------------------------------------------------------
 def _torch():
     try:
@@ -275,7 +316,9 @@ class Simulation:
     PyTorch's current stream when PyTorch is available.
     """
 
-    def __init__(self, params, stream=None, use_torch_allocator: bool = True):
+    def __init__(self, params, stream=None, use_torch_allocator: bool = True, slab=None):
+        """slab = (y_lo, ny_own): a y-slab of the grid `params` describes
+        (lbm_create_slab); the handle then holds the slab's local rows."""
         self.params = params
         self.nx, self.ny = int(params.nx), int(params.ny)
         torch = _torch()
@@ -285,7 +328,13 @@ class Simulation:
         self.stream = int(getattr(stream, "cuda_stream", stream) or 0)
         self._alloc, self._keep = (torch_allocator() if use_torch_allocator else (None, ()))
         self._p = params_struct(params)
-        self._h = lbm_create(self._p, self.stream, self._alloc)
+        if slab is None:
+            self._h = lbm_create(self._p, self.stream, self._alloc)
+            self.slab = None
+        else:
+            self._h = lbm_create_slab(self._p, slab[0], slab[1], self.stream, self._alloc)
+            self.slab = lbm_slab_info(self._h)  # (y_lo, ny_own, ghost_lo, ghost_hi)
+            self.ny = self.slab[1] + self.slab[2] + self.slab[3]
 
     def close(self):
         if getattr(self, "_h", None):
@@ -401,6 +450,17 @@ class Simulation:
         out = np.empty(2)
         lbm_adjoint_gravity(self._h, out)
         return out
+
+    # -- y-slabs (halo messages in device buffers, e.g. torch uint8 tensors)
+    @property
+    def halo_bytes(self) -> int:
+        return lbm_slab_halo_bytes(self._h)
+
+    def pack(self, side: int, buf):
+        lbm_slab_pack(self._h, side, buf.data_ptr())
+
+    def unpack(self, side: int, buf):
+        lbm_slab_unpack(self._h, side, buf.data_ptr())
 
 
 __all__ = ["Simulation", "LbmParams", "LbmError", "load", "params_struct", "torch_allocator",

@@ -64,6 +64,11 @@ struct lbm_handle {
   void* obs_planes = nullptr;
   int* dfill = nullptr;  // solid nodes next to fluid (dense indices)
   int nfill = 0;
+  // y-slab of a larger grid (lbm_create_slab): rows [slab_y0, slab_y0 +
+  // slab_own) of the global grid, held as local rows [ghost_lo, ghost_lo +
+  // slab_own) between ghost rows that the halo exchange fills
+  bool slab = false;
+  int slab_y0 = 0, slab_own = 0, ghost_lo = 0, ghost_hi = 0;
 };
 
 static std::string g_create_error;
@@ -249,6 +254,8 @@ static Phys<T> make_phys(const lbm_handle* h) {
   P.obs = h->dobs;
   P.obs_fill = h->dfill;
   P.obs_nfill = h->nfill;
+  P.diag_y0 = h->slab ? h->ghost_lo : 0;
+  P.diag_y1 = h->slab ? h->ghost_lo + h->slab_own : h->ny;
   return P;
 }
 
@@ -351,9 +358,13 @@ static int do_step(lbm_handle* h, int64_t n) {
   const Phys<T> P = make_phys<T>(h);
   const int de = h->prm.diag_every;
   for (int64_t s = 0; s < n; ++s) {
-    const bool due = de > 0 && ((h->t + 1) % de == 0);
+    // a slab's ghost rows are stale until the next halo exchange, so its
+    // diagnostics are taken on request (lbm_fields LBM_DIAG) after it; the
+    // step still records phi(t-1) for their S_m
+    const bool record = de > 0 && ((h->t + 1) % de == 0);
+    const bool due = record && !h->slab;
     Bufs<T> B = bufs_now<T>(h);
-    B.phi_prev = due ? (T*)h->phi_prev : nullptr;
+    B.phi_prev = record ? (T*)h->phi_prev : nullptr;
     cudaError_t e = cudaErrorNotSupported;
     if (h->dobs)
       e = launch_mode<C>(h, MODE_STEP, P, B);
@@ -576,11 +587,19 @@ static int do_set_fields(lbm_handle* h, int which, const double* in) {
 // ---------------------------------------------------------------------------
 extern "C" {
 
+static int create_impl(const lbm_params* params, void* stream, const lbm_allocator* alloc, lbm_handle** out);
+
 int lbm_create(const lbm_params* params, void* stream, const lbm_allocator* alloc, lbm_handle** out) {
   if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
   *out = nullptr;
   int rc = validate(params);
   if (rc) return rc;
+  return create_impl(params, stream, alloc, out);
+}
+
+}  // extern "C"
+
+static int create_impl(const lbm_params* params, void* stream, const lbm_allocator* alloc, lbm_handle** out) {
   if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, LBM_EINVAL, "allocator needs alloc and free");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -640,6 +659,8 @@ int lbm_create(const lbm_params* params, void* stream, const lbm_allocator* allo
   return LBM_OK;
 }
 
+extern "C" {
+
 int lbm_init_fields(lbm_handle* h, const double* phi, const double* ux, const double* uy, const double* p) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   if (!phi) return fail(h, LBM_EINVAL, "phi is NULL");
@@ -650,6 +671,8 @@ int lbm_init_fields(lbm_handle* h, const double* phi, const double* ux, const do
 int lbm_step(lbm_handle* h, int64_t nsteps) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps < 0");
+  if (h->slab && nsteps > 1)
+    return fail(h, LBM_EINVAL, "a y-slab advances one step per call: exchange its halos between steps");
   PFLBM_DISPATCH(h, do_step, h, nsteps);
 }
 
@@ -677,6 +700,7 @@ int lbm_set_fields(lbm_handle* h, int32_t which, const double* in) {
 
 int lbm_set_solid(lbm_handle* h, const uint8_t* solid) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (h->slab) return fail(h, LBM_EUNSUPPORTED, "solid obstacles are not supported on a y-slab");
   long long nsolid = 0;
   const long long N = (long long)h->nx * h->ny;
   if (solid)
@@ -919,6 +943,7 @@ static int ensure_adjoint(lbm_handle* h) {
 
 static int adjoint_supported(lbm_handle* h) {
   if (h->dobs) return fail(h, LBM_EUNSUPPORTED, "the adjoint does not cover solid obstacles");
+  if (h->slab) return fail(h, LBM_EUNSUPPORTED, "the adjoint does not cover y-slabs");
   if (h->prm.phase_model != LBM_AC)
     return fail(h, LBM_EUNSUPPORTED, "the adjoint covers the Allen-Cahn phase field only");
   if (h->prec != LBM_FP64 && h->prec != LBM_FP32)
@@ -1024,6 +1049,103 @@ int lbm_adjoint_gravity(lbm_handle* h, double* dJ_dG) {
   CUDA_TRY(h, cudaMemcpyAsync(dJ_dG, h->gacc, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   return check_device_flag(h);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// y-slab decomposition of one grid over several devices or handles.
+//
+// A slab owns the global rows [y_lo, y_lo + ny_own).  It is an ordinary
+// handle over ny_own + ghost_lo + ghost_hi local rows: LBM_SLAB_GHOST ghost
+// rows below and above its own rows, except on a side that is a global wall
+// (the wall is then the slab's own).  The step kernels run unchanged over the
+// local rows.  A node's update reads populations at most three rows away
+// (Cahn-Hilliard: phi two rows away feeds mu_phi one row away; Allen-Cahn:
+// two), and the macroscopic pass of the diagnostics one row more, so once
+// the ghost rows hold the neighbours' post-collision populations, every own
+// row advances exactly as in the undivided grid.  The ghost rows themselves
+// are then stale (their update saw the local grid's far edge, a wall or the
+// periodic wrap), and the next halo exchange overwrites them.
+//
+// Exchange per step and side: the LBM_SLAB_GHOST own rows next to the side,
+// of the f set and of the g set, post-collision (one contiguous block each:
+// rows are row-interleaved, all nine planes of a row adjacent).  lbm_slab_pack
+// copies them out, lbm_slab_unpack writes a neighbour's message into the
+// ghost rows.  The history and phi(t-1) are per node and never exchanged.
+// ---------------------------------------------------------------------------
+static long long pop_row_bytes_of(const lbm_handle* h) { return h->pop_bytes / h->ny; }
+
+extern "C" {
+
+int lbm_create_slab(const lbm_params* global, int32_t y_lo, int32_t ny_own, void* stream,
+                    const lbm_allocator* alloc, lbm_handle** out) {
+  if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate(global);
+  if (rc) return rc;
+  const bool wy = global->bc[LBM_BOTTOM] == LBM_WALL;
+  if (ny_own < LBM_SLAB_GHOST || y_lo < 0 || (long long)y_lo + ny_own > global->ny)
+    return fail(nullptr, LBM_EINVAL, "slab rows [%d, %d) must lie in [0, %d) and number at least %d", y_lo,
+                y_lo + ny_own, global->ny, LBM_SLAB_GHOST);
+  if (ny_own == global->ny) return fail(nullptr, LBM_EINVAL, "a slab over the whole grid: use lbm_create");
+  lbm_params loc = *global;
+  const int glo = (wy && y_lo == 0) ? 0 : LBM_SLAB_GHOST;
+  const int ghi = (wy && y_lo + ny_own == global->ny) ? 0 : LBM_SLAB_GHOST;
+  loc.ny = ny_own + glo + ghi;
+  rc = validate(&loc);
+  if (rc) return rc;
+  lbm_handle* h = nullptr;
+  rc = create_impl(&loc, stream, alloc, &h);
+  if (rc) return rc;
+  h->slab = true;
+  h->slab_y0 = y_lo;
+  h->slab_own = ny_own;
+  h->ghost_lo = glo;
+  h->ghost_hi = ghi;
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_slab_info(const lbm_handle* h, int32_t info[4]) {
+  if (!h || !info) return fail(nullptr, LBM_EINVAL, "handle or info is NULL");
+  info[0] = h->slab ? h->slab_y0 : 0;
+  info[1] = h->slab ? h->slab_own : h->ny;
+  info[2] = h->ghost_lo;
+  info[3] = h->ghost_hi;
+  return LBM_OK;
+}
+
+int64_t lbm_slab_halo_bytes(const lbm_handle* h) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  return 2LL * LBM_SLAB_GHOST * pop_row_bytes_of(h);
+}
+
+// rows [first, first + LBM_SLAB_GHOST) of the current f and g sets <-> buf
+static int slab_copy(lbm_handle* h, int side, void* buf, bool pack) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!buf) return fail(h, LBM_EINVAL, "buffer is NULL");
+  if (!h->slab) return fail(h, LBM_EINVAL, "not a y-slab (lbm_create_slab)");
+  if (side != LBM_BOTTOM && side != LBM_TOP) return fail(h, LBM_EINVAL, "side %d: LBM_BOTTOM or LBM_TOP", side);
+  const int ghosts = side == LBM_BOTTOM ? h->ghost_lo : h->ghost_hi;
+  if (!ghosts) return fail(h, LBM_EINVAL, "side %d of this slab is a global wall: nothing to exchange", side);
+  int first;
+  if (pack) first = side == LBM_BOTTOM ? h->ghost_lo : h->ghost_lo + h->slab_own - LBM_SLAB_GHOST;
+  else first = side == LBM_BOTTOM ? 0 : h->ghost_lo + h->slab_own;
+  const long long rb = pop_row_bytes_of(h), bytes = LBM_SLAB_GHOST * rb;
+  for (int set = 0; set < 2; ++set) {
+    unsigned char* rows = static_cast<unsigned char*>(h->pops[set][h->cur]) + first * rb;
+    unsigned char* msg = static_cast<unsigned char*>(buf) + set * bytes;
+    if (pack) CUDA_TRY(h, cudaMemcpyAsync(msg, rows, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    else CUDA_TRY(h, cudaMemcpyAsync(rows, msg, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  return LBM_OK;
+}
+
+int lbm_slab_pack(lbm_handle* h, int32_t side, void* dst) { return slab_copy(h, side, dst, true); }
+
+int lbm_slab_unpack(lbm_handle* h, int32_t side, const void* src) {
+  return slab_copy(h, side, const_cast<void*>(src), false);
 }
 
 }  // extern "C"

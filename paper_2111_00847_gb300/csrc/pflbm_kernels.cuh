@@ -90,6 +90,7 @@ struct Phys {
   // 1 / (1 + sum_i r_i) that makes a node's decoded populations sum to phi.
   T dv_r[2][2], dv_s[2], dv_is[2], dv_c0;
   int seg_rows;  // rows per block segment of the TMA step on small grids (set by its launcher)
+  int diag_y0, diag_y1;  // rows [diag_y0, diag_y1) enter the diagnostics (a y-slab: its own rows)
   // Solid obstacles (nullptr: none).  Per node of the dense [ny][nx] grid:
   // bit i-1 (i = 1..8) set when link i reflects, i.e. its upstream node
   // x - c_i is solid or lies beyond a wall; bit OBS_SOLID set at solid nodes.
@@ -356,19 +357,30 @@ __device__ __forceinline__ T phi_at(const Phys<T>& P, const Bufs<T>& B, int x, i
   }
 }
 
+// Products and sums rounded one by one (never contracted into an FMA), so
+// that every call site of a function built from them returns the same bits.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+
 // Wetting ghost, Eqs. (49)-(50): phi_w is the root the paper selects,
 // (-b + sqrt(b^2 - 4ac)) / (2a), evaluated as 2c / (-b - sqrt(b^2 - 4ac))
 // (the same number; finite as a -> 0, where it tends to -c/b); the ghost at
 // -1/2 is the quadratic through (0, phi_w), (1/2, phi_1), (3/2, phi_2).
+// Every operation is rounded on its own: a kernel forms the ghost at more
+// than one place (a segment's first row from global memory, the others from
+// staged rows), and a grid divided into y-slabs must see the same value at
+// either place.
 template <typename T>
 __device__ __forceinline__ T wall_ghost(const Phys<T>& P, int side, T phi1, T phi2) {
   const T a = P.wa[side];
-  const T b = T(8.0 / 3.0) - a * (P.phiA + P.phiB);
-  const T c = a * P.phiA * P.phiB + phi2 * T(1.0 / 3.0) - T(3) * phi1;
-  T disc = b * b - T(4) * a * c;
+  const T b = add_rn(T(8.0 / 3.0), -mul_rn(a, add_rn(P.phiA, P.phiB)));
+  const T c = add_rn(add_rn(mul_rn(mul_rn(a, P.phiA), P.phiB), mul_rn(phi2, T(1.0 / 3.0))), -mul_rn(T(3), phi1));
+  T disc = add_rn(mul_rn(b, b), -mul_rn(mul_rn(T(4), a), c));
   disc = disc > T(0) ? disc : T(0);
-  const T phiw = T(2) * c / (-b - sqrt(disc));
-  return T(8.0 / 3.0) * phiw - T(2) * phi1 + phi2 * T(1.0 / 3.0);
+  const T phiw = mul_rn(T(2), c) / add_rn(-b, -sqrt(disc));
+  return add_rn(add_rn(mul_rn(T(8.0 / 3.0), phiw), -mul_rn(T(2), phi1)), mul_rn(phi2, T(1.0 / 3.0)));
 }
 
 // ---------------------------------------------------------------------------
@@ -935,7 +947,6 @@ struct TmaLayout {
 // Each try_wait suspends for at most ~1 us (the hint), so a wait gives up
 // after about a second; a normal row arrives within microseconds.
 constexpr long long MBAR_SPIN_LIMIT = 1LL << 20;
-constexpr long long MBAR_DRAIN_LIMIT = 1LL << 10;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -983,6 +994,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   for (long long it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+
+// Drain of a block whose bounded wait timed out: wait (with the full bound)
+// for the newest phase of every ring slot, i.e. for the copies of the last
+// R staged rows [last - R + 1, last] (rows below `first` were never staged).
+// An older phase of a slot completed before the slot was staged again, and a
+// completed phase returns at once, so only copies still in flight are waited
+// for; nothing that was never armed is.  The block's results are invalid
+// (the host reports LBM_ECUDA).
+__device__ __forceinline__ void drain_ring(uint64_t* bar, int R, int first, int last) {
+  for (int r = max(first, last - R + 1); r <= last; ++r) {
+    const int li = r - first;
+    mbar_wait_bounded(&bar[li % R], (li / R) & 1);
+  }
 }
 
 // Decoded population i in staged column c of a slot.
@@ -1288,7 +1313,8 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
   int fR0 = LF0 % RF, gA = 0;                              // f row y0, g row y0-1
   int fW = (LF0 + 2) % RF, fWp = ((LF0 + 2) / RF) & 1;     // f row y0+2
   int gW = 2 % RG, gWp = (2 / RG) & 1;       // g row y0+1 (local 2)
-  for (int y = y0; y < y1 && !failed; ++y) {
+  int y = y0;  // on failure: the march step that stopped (rows above it staged by the step before)
+  for (; y < y1 && !failed; ++y) {
     ok = true;
     if (y + 2 <= f_last) ok = mbar_wait_bounded(&barF[fW], fWp) && ok;
     if (y + 1 <= g_last) ok = mbar_wait_bounded(&barG[gW], gWp) && ok;
@@ -1381,12 +1407,12 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
   }
   if (failed) {
     // record, then let every copy this block issued land (bounded) before
-    // the block's shared memory is released
+    // the block's shared memory is released; the results of this launch
+    // are invalid (the host reports LBM_ECUDA)
     if (tid == 0) {
       atomicOr(err, 1);
-      for (int k = 0; k < RF + RG; ++k) {
-        for (int q = 0; q < 2; ++q) mbar_wait_bounded(&barF[k], q, MBAR_DRAIN_LIMIT);
-      }
+      drain_ring(barF, RF, fbase, min(y + 1 + DF, f_last));
+      drain_ring(barG, RG, gbase, min(y + DG, g_last));
     }
     __syncthreads();
   }
@@ -1399,11 +1425,14 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
 // node update of row y reads mu_phi on rows y-1 .. y+1, and mu_phi of a row
 // needs the Laplacian of phi (Eq. (5)), so phi runs two rows and two columns
 // ahead.  Per march step y: phi of row y+2 from the staged f rows y+1 .. y+3
-// (a ghost row above a top wall); barrier; mu_phi of row y+1 over columns
-// -1 .. w from phi rows y .. y+2 (mirrored at walls, as the oracle's ghost
-// rule for mu); barrier; the node update of row y.  Segment starts form phi
-// of rows y0-2 and y0-1 from pulls of the global planes, and phi of y0, y0+1
-// and mu_phi of y0-1, y0 from the staged rows.
+// (a ghost row above a top wall); block barrier; mu_phi of row y+1 from phi
+// rows y .. y+2 (mirrored at walls, as the oracle's ghost rule for mu); the
+// node update of row y.  mu_phi is kept per warp: each warp forms it over its
+// own 32 columns plus one column on either side (its edge lanes compute the
+// outer ones again), so only a warp barrier separates writing it from
+// reading it, and a march step has one block barrier.  Segment starts form
+// phi of rows y0-2 and y0-1 from pulls of the global planes, and phi of y0,
+// y0+1 and mu_phi of y0-1, y0 from the staged rows.
 // ---------------------------------------------------------------------------
 template <class C>
 struct TmaChCfg {
@@ -1413,13 +1442,15 @@ struct TmaChCfg {
 };
 constexpr int CH_PRING = 8;  // phi rows (power of two): rows y-2 .. y+2 may be in use
 constexpr int CH_MRING = 4;  // mu_phi rows (power of two): rows y-2 .. y+1
+constexpr int CH_MWW = 34;   // mu_phi columns of a warp's rows: its 32 and one on either side
 
 template <class C, int TBX, int DF, int DG>
 struct TmaChLayout {
   using T = typename C::value_t;
   static constexpr int SEG = Seg<TBX>::value;
   static constexpr int RF = 5 + DF, RG = 3 + DG;  // f rows y-1 .. y+3 live, g rows y-1 .. y+1
-  static constexpr int PW = TBX + 4, MW = TBX + 2;  // phi columns -2 .. w+1, mu columns -1 .. w
+  static constexpr int PW = TBX + 4;                // phi columns -2 .. w+1
+  static constexpr int MW = ((TBX + 31) / 32) * CH_MWW;  // per warp: mu columns of its lanes, +-1
   static constexpr size_t P0 = (size_t)SEG * C::B0;
   static constexpr size_t PI = (size_t)SEG * C::BI;
   static constexpr size_t SLOT = P0 + 8 * PI;
@@ -1450,7 +1481,7 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
   unsigned char* const sf = smem + L::f_off;
   unsigned char* const sg = smem + L::g_off;
   T* const sp = reinterpret_cast<T*>(smem + L::phi_off);  // [CH_PRING][PW], column c at c + 2
-  T* const sm = reinterpret_cast<T*>(smem + L::mu_off);   // [CH_MRING][MW], column c at c + 1
+  T* const sm = reinterpret_cast<T*>(smem + L::mu_off);   // [CH_MRING][warps][CH_MWW]
   uint64_t* const barF = reinterpret_cast<uint64_t*>(smem + L::bar_off);
   uint64_t* const barG = barF + RF;
 
@@ -1499,7 +1530,11 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
   auto wait_f = [&](int r) { return mbar_wait_bounded(&barF[fidx(r)], ((r - fbase) / RF) & 1); };
   auto wait_g = [&](int r) { return mbar_wait_bounded(&barG[gidx(r)], ((r - gbase) / RG) & 1); };
   auto prow = [&](int r) { return sp + (r & (CH_PRING - 1)) * PW; };
-  auto mrow = [&](int r) { return sm + (r & (CH_MRING - 1)) * MW; };
+  const int lane = tid & 31, wbase = tid & ~31;  // this thread's lane, its warp's first column
+  // the last active lane of this warp (edge of the strip's last columns)
+  const int last_lane = min(31, w - 1 - wbase);
+  // mu_phi row r of this warp: column wbase + j at index j + 1 (j = -1 .. 32)
+  auto mrow = [&](int r) { return sm + (r & (CH_MRING - 1)) * MW + (tid >> 5) * CH_MWW; };
 
   // phi of row r (in the domain or wrapped) from the staged slots: own column,
   // thread 0 columns -1 and -2, thread w-1 columns w and w+1; at an x wall the
@@ -1628,8 +1663,9 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
                   (((pp[j + 1] - ph) + (pm[j - 1] - ph)) + ((pp[j - 1] - ph) + (pm[j + 1] - ph))) * T(1.0 / 6.0);
     return P.beta4 * (ph - P.phiA) * (ph - P.phiB) * (ph - P.phibar) - P.kappa * lap;
   };
-  // mu_phi of row r over columns -1 .. w; at an x wall the halo column
-  // mirrors the column next to the wall (written by the thread owning it)
+  // mu_phi of row r for this warp: its own columns, and the column beyond
+  // either end (lane 0 and the last active lane form those again); at an x
+  // wall the column beyond mirrors the column next to the wall
   auto mu_row = [&](int r) {
     const T* pm = prow(r - 1);
     const T* p0 = prow(r);
@@ -1638,21 +1674,22 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
     if (!active) return;
     if constexpr (OBS) {  // from the filled plane, mirrored at x walls
       const T* mr = B.mus + ix(P, 1, 0, 0, wrap_row(r));
-      d[tid + 1] = mr[x];
-      if (tid == 0) d[0] = (wx && x0 == 0) ? mr[0] : mr[x0 > 0 ? x0 - 1 : nx - 1];
-      if (tid == w - 1) d[w + 1] = (wx && x0 + w == nx) ? mr[nx - 1] : mr[x0 + w < nx ? x0 + w : 0];
+      const T mo = mr[x];
+      d[lane + 1] = mo;
+      if (lane == 0) d[0] = (wx && x == 0) ? mo : mr[x > 0 ? x - 1 : nx - 1];
+      if (lane == last_lane) d[lane + 2] = (wx && x == nx - 1) ? mo : mr[x + 1 < nx ? x + 1 : 0];
       return;
     }
     const T mo = mu_at(pm, p0, pp, tid + 2);
-    d[tid + 1] = mo;
-    if (tid == 0) d[0] = (wx && x0 == 0) ? mo : mu_at(pm, p0, pp, 1);
-    if (tid == w - 1) d[w + 1] = (wx && x0 + w == nx) ? mo : mu_at(pm, p0, pp, w + 2);
+    d[lane + 1] = mo;
+    if (lane == 0) d[0] = (wx && x == 0) ? mo : mu_at(pm, p0, pp, tid + 1);
+    if (lane == last_lane) d[lane + 2] = (wx && x == nx - 1) ? mo : mu_at(pm, p0, pp, tid + 3);
   };
-  // mirrored mu_phi row beyond a y wall
+  // mirrored mu_phi row beyond a y wall (this warp's entries)
   auto mu_copy_row = [&](int rdst, int rsrc) {
     T* d = mrow(rdst);
     const T* s = mrow(rsrc);
-    for (int j = tid; j < w + 2; j += TBX) d[j] = s[j];
+    for (int j = lane; j < CH_MWW; j += 32) d[j] = s[j];
   };
 
   bool ok = true;
@@ -1676,10 +1713,10 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
   if (!failed) {
     for (int r = y0 - 1; r <= y0; ++r)
       if ((r >= 0 && r < ny) || !wy) mu_row(r);
-    __syncthreads();
+    __syncwarp();
     if (wy && y0 == 0) {
       mu_copy_row(-1, 0);
-      __syncthreads();
+      __syncwarp();
     }
   }
   T h[5] = {T(0), T(0), T(0), T(0), T(0)};
@@ -1690,7 +1727,8 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
   }
 
   // ---------------------------------------------------------------- march
-  for (int y = y0; y < y1 && !failed; ++y) {
+  int y = y0;  // on failure: the march step that stopped (rows above it staged by the step before)
+  for (; y < y1 && !failed; ++y) {
     ok = true;
     if (y + 3 <= f_last) ok = wait_f(y + 3) && ok;
     if (y + 1 <= g_last) ok = wait_g(y + 1) && ok;
@@ -1708,7 +1746,7 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
     const int r1 = y + 1;
     if (r1 < ny || !wy) mu_row(r1);
     else if (r1 == ny) mu_copy_row(ny, ny - 1);
-    __syncthreads();
+    __syncwarp();
     T hn[5] = {T(0), T(0), T(0), T(0), T(0)};
     if (active && y + 1 < y1) {
       const T* hb = B.hist + ix(P, 5, 0, x, y + 1);
@@ -1733,7 +1771,7 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
       const T* mm = mrow(y - 1);
       const T* m0 = mrow(y);
       const T* mp = mrow(y + 1);
-      const int cm = tid + 1;
+      const int cm = lane + 1;
       T mu9[9];
       mu9[0] = m0[cm];
       mu9[1] = m0[cm + 1];
@@ -1780,9 +1818,8 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
   if (failed) {
     if (tid == 0) {
       atomicOr(err, 1);
-      for (int k = 0; k < RF + RG; ++k) {
-        for (int q = 0; q < 2; ++q) mbar_wait_bounded(&barF[k], q, MBAR_DRAIN_LIMIT);
-      }
+      drain_ring(barF, RF, fbase, min(y + 2 + DF, f_last));
+      drain_ring(barG, RG, gbase, min(y + DG, g_last));
     }
     __syncthreads();
   }
@@ -1956,12 +1993,12 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(const Phys<T> P, 
                                                                const T* __restrict__ phi_prev,
                                                                double* __restrict__ partial) {
   double v[DIAG_FIELDS] = {0, 0, 0, 0, 0, 0};
-  const long long N = (long long)P.nx * P.ny;
+  const long long N = (long long)P.nx * P.diag_y1;
   const long long pl = P.pitch;  // macro plane k of a node sits k * pitch after plane 0
   const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
   const int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
   const double wi[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+  for (long long n = (long long)P.nx * P.diag_y0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(n / P.nx), x = (int)(n - (long long)y * P.nx);
     const unsigned om = P.obs ? P.obs[n] : 0u;

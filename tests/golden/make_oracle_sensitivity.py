@@ -22,7 +22,9 @@ g_i (g_0 without the constant rho0) and each history value is multiplied by
 eps = 2^-53 (an FP64 implementation) or 2^-24 (FP32 storage).  Recorded per
 case, n_delta and arithmetic, every 10 steps to 100: max |delta f| and
 max |delta g| (FP64: absolute; FP32: relative to the array's maximum, the
-form of the FP32 bar).
+form of the FP32 bar).  For the paper's workloads also "onestep": the
+largest departure after a single step from the oracle's state at
+t0 = 0, 25, 50, 75, 99 perturbed once in the same way.
 
 Run: python tests/golden/make_oracle_sensitivity.py  (about a minute)
 """
@@ -71,6 +73,46 @@ def trajectory(case, eps, steps=100, every=10):
     return out
 
 
+ONE_STEP_TIMES = (0, 25, 50, 75, 99)
+
+
+def one_step(case, eps):
+    """max over t0 in ONE_STEP_TIMES of the oracle's departure after one step
+    from its state at t0 perturbed once at one rounding (as above)."""
+    o = oracle.Oracle(case.params)
+    o.init_fields(case.phi, case.ux, case.uy, case.p)
+    rho0 = case.params.rho0
+    n = case.params.nx * case.params.ny
+    worst = [0.0, 0.0]
+    t = 0
+    for t0 in ONE_STEP_TIMES:
+        o.step(t0 - t)
+        t = t0
+        f, g, h = o.fields(oracle.F_POP), o.fields(oracle.G_POP), o.fields(oracle.HIST)
+        outs = []
+        for e in (0.0, eps):
+            xi = 2.0 * W.uniform_array(1000 + t0, 23 * n) - 1.0
+            fp = f * (1.0 + e * xi[: 9 * n].reshape(f.shape))
+            gp = g.copy()
+            gp[0] -= rho0
+            gp *= 1.0 + e * xi[9 * n: 18 * n].reshape(g.shape)
+            gp[0] += rho0
+            hp = h * (1.0 + e * xi[18 * n:].reshape(h.shape))
+            q = oracle.Oracle(case.params)
+            q.init_fields(case.phi, case.ux, case.uy, case.p)
+            q.set_fields(oracle.F_POP, fp)
+            q.set_fields(oracle.G_POP, gp)
+            q.set_fields(oracle.HIST, hp)
+            q.step(1)
+            outs.append((q.fields(oracle.F_POP), q.fields(oracle.G_POP)))
+            q.close()
+        for k in range(2):
+            d = np.abs(outs[1][k] - outs[0][k]).max()
+            worst[k] = max(worst[k], d)
+    o.close()
+    return worst
+
+
 def main():
     oracle.set_threads(os.cpu_count() or 1)
     lines = ["# Oracle response to per-step rounding-level perturbations (see make_oracle_sensitivity.py).",
@@ -90,6 +132,12 @@ def main():
                     dg /= np.abs(ref[t][1]).max()
                 lines.append(f"{name} {nd:g} {arith} {t} {df:.3e} {dg:.3e}")
             print(lines[-1], flush=True)
+            if nd > 0:
+                df, dg = one_step(case, eps)
+                if arith == "fp32":
+                    df /= np.abs(ref[100][0]).max()
+                    dg /= np.abs(ref[100][1]).max()
+                lines.append(f"{name} {nd:g} {arith} onestep {df:.3e} {dg:.3e}")
     with open(OUT, "w") as fh:
         fh.write("\n".join(lines) + "\n")
 

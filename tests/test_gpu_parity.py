@@ -58,9 +58,9 @@ def rel_err(a, b, rho0=None):
 # (rho0 removed) is printed beside it and held to TOL32_GDYN: it is driven by
 # mu_phi grad phi, and mu_phi = psi'(phi) - k lap phi differences phi values
 # that FP32 storage of the nine f_i rounds at ~5e-8, a ~1e-5 relative
-# effect on mu.
+# effect on mu (measured on GB300: at most 1.3e-5, the layered channel).
 TOL32 = 1e-5
-TOL32_GDYN = 2e-4
+TOL32_GDYN = 5e-5
 
 
 def _cmp_pops(pk, oracle_mod, sim, o, fp64, tol64=1e-12, tol32=(TOL32, TOL32), label=""):
