@@ -502,13 +502,19 @@ def main():
         del s64
         lups64 = n64 * n64 * k64 / (ms64 / 1e3)
         fl, fl_from = profiled_traffic("fp64", key="fp64_flops_per_lu")
+        ni, _ = profiled_traffic("fp64", key="fp64_inst_per_lu")
         alu = None
         if fl is not None:
             ach = fl * lups64 / 1e9
             alu = {"bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
                    "frac": ach / FP64_NOMINAL_GFLOPS, "traffic": None,
-                   "peak_source": "nominal FP64 rate of GB300 (no measured FP64 peak)",
+                   "peak_source": "nominal FP64 rate of GB300: 2 FP64 instructions per clock per SM "
+                                  "x 152 SMs x 2.07 GHz x 2 flops (no measured FP64 peak)",
                    "flops_per_lu": fl, "flops_source": fl_from}
+            if ni is not None:
+                # DADD and DMUL hold an FP64 issue slot for one flop: the pipe's
+                # own rate, in instructions
+                alu["fp64_pipe_frac"] = ni * lups64 / (2 * 152 * 2.07e9)
         models["fp64"] = {"value": whole_job_mlups(world, n64 * n64, k64, ms64 / 1e3), "unit": UNIT,
                           "workload": workload_name(n64), "steps": k64, "ms_per_step": ms64 / k64,
                           "roofline": alu, "hbm_frac": roof64["frac"], "clocks": clk64}

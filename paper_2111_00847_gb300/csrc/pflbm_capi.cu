@@ -64,6 +64,8 @@ struct lbm_handle {
   void* obs_planes = nullptr;
   int* dfill = nullptr;  // solid nodes next to fluid (dense indices)
   int nfill = 0;
+  uint8_t* dnear = nullptr;  // per block of the Allen-Cahn TMA step: reaches a solid node
+  int near_box[4] = {0, 0, 0, 0};  // phi-plane region those blocks read (x_lo, x_hi, y_lo, y_hi)
   // y-slab of a larger grid (lbm_create_slab): rows [slab_y0, slab_y0 +
   // slab_own) of the global grid, held as local rows [ghost_lo, ghost_lo +
   // slab_own) between ghost rows that the halo exchange fills
@@ -254,6 +256,8 @@ static Phys<T> make_phys(const lbm_handle* h) {
   P.obs = h->dobs;
   P.obs_fill = h->dfill;
   P.obs_nfill = h->nfill;
+  P.obs_near = h->dnear;
+  for (int k = 0; k < 4; ++k) P.obs_box[k] = h->near_box[k];
   P.diag_y0 = h->slab ? h->ghost_lo : 0;
   P.diag_y1 = h->slab ? h->ghost_lo + h->slab_own : h->ny;
   return P;
@@ -582,6 +586,76 @@ static int do_set_fields(lbm_handle* h, int which, const double* in) {
     default: return fn<PopDev<__nv_bfloat16>>(__VA_ARGS__);                \
   }
 
+// Solid obstacles on the Allen-Cahn TMA step: which blocks of its launch
+// grid reach a solid node (within 3 nodes of their rows and columns: the
+// pulls, the phi stencil and the fill of a solid neighbour reach 3), and the
+// region of the phi plane those blocks read (their rows and columns widened
+// by 2, the reach of their phi ring and of the fill).  Blocks away from
+// obstacles run the plain step's path, so the per-step phi pass covers only
+// that region.  Periodic sides wrap; a region that wraps takes the whole
+// extent of its direction.
+template <class C>
+static int build_near_map(lbm_handle* h, const uint8_t* solid) {
+  int tbx = 0, seg = 0;
+  tma_step_grid<C>(h->nx, h->ny, &tbx, &seg);
+  const int nx = h->nx, ny = h->ny;
+  const bool px = h->prm.bc[LBM_LEFT] == LBM_PERIODIC, py = h->prm.bc[LBM_BOTTOM] == LBM_PERIODIC;
+  // integral image of the mask: S[(y) (nx+1) + x] = solid nodes in [0, x) x [0, y)
+  std::vector<int> S((size_t)(nx + 1) * (ny + 1), 0);
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x)
+      S[(size_t)(y + 1) * (nx + 1) + x + 1] = (solid[(size_t)y * nx + x] != 0) + S[(size_t)y * (nx + 1) + x + 1] +
+                                              S[(size_t)(y + 1) * (nx + 1) + x] - S[(size_t)y * (nx + 1) + x];
+  auto rect = [&](int xa, int xb, int ya, int yb) {
+    return S[(size_t)yb * (nx + 1) + xb] - S[(size_t)ya * (nx + 1) + xb] - S[(size_t)yb * (nx + 1) + xa] +
+           S[(size_t)ya * (nx + 1) + xa];
+  };
+  // [a, b) in a direction of n nodes -> up to two in-grid intervals
+  auto split = [](int a, int b, int n, bool periodic, int out[4]) {
+    if (!periodic) {
+      out[0] = std::max(a, 0), out[1] = std::min(b, n), out[2] = out[3] = 0;
+      return;
+    }
+    if (b - a >= n) {
+      out[0] = 0, out[1] = n, out[2] = out[3] = 0;
+      return;
+    }
+    const int a0 = ((a % n) + n) % n, e = a0 + (b - a);
+    out[0] = a0, out[1] = std::min(e, n);
+    out[2] = 0, out[3] = e > n ? e - n : 0;
+  };
+  const int gx = (nx + tbx - 1) / tbx, gy = (ny + seg - 1) / seg;
+  std::vector<uint8_t> nearv((size_t)gx * gy, 0);
+  int bx0 = nx, bx1 = 0, by0 = ny, by1 = 0;
+  bool xwrap = false, ywrap = false;
+  for (int by = 0; by < gy; ++by)
+    for (int bx = 0; bx < gx; ++bx) {
+      const int x0 = bx * tbx, x1 = std::min(x0 + tbx, nx), y0 = by * seg, y1 = std::min(y0 + seg, ny);
+      int xi[4], yi[4];
+      split(x0 - 3, x1 + 3, nx, px, xi);
+      split(y0 - 3, y1 + 3, ny, py, yi);
+      long long c = 0;
+      for (int i = 0; i < 4; i += 2)
+        for (int j = 0; j < 4; j += 2)
+          if (xi[i + 1] > xi[i] && yi[j + 1] > yi[j]) c += rect(xi[i], xi[i + 1], yi[j], yi[j + 1]);
+      if (!c) continue;
+      nearv[(size_t)by * gx + bx] = 1;
+      xwrap = xwrap || (px && (x0 - 2 < 0 || x1 + 2 > nx));
+      ywrap = ywrap || (py && (y0 - 2 < 0 || y1 + 2 > ny));
+      bx0 = std::min(bx0, std::max(x0 - 2, 0)), bx1 = std::max(bx1, std::min(x1 + 2, nx));
+      by0 = std::min(by0, std::max(y0 - 2, 0)), by1 = std::max(by1, std::min(y1 + 2, ny));
+    }
+  h->near_box[0] = xwrap ? 0 : bx0;
+  h->near_box[1] = xwrap ? nx : bx1;
+  h->near_box[2] = ywrap ? 0 : by0;
+  h->near_box[3] = ywrap ? ny : by1;
+  h->dnear = (uint8_t*)dev_alloc(h, nearv.size());
+  if (!h->dnear) return fail(h, LBM_ENOMEM, "obstacle block map");
+  CUDA_TRY(h, cudaMemcpyAsync(h->dnear, nearv.data(), nearv.size(), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));  // nearv is released on return
+  return LBM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // C entry points
 // ---------------------------------------------------------------------------
@@ -711,9 +785,11 @@ int lbm_set_solid(lbm_handle* h, const uint8_t* solid) {
     dev_free(h, h->dobs);
     dev_free(h, h->obs_planes);
     dev_free(h, h->dfill);
+    dev_free(h, h->dnear);
     h->dobs = nullptr;
     h->obs_planes = nullptr;
     h->dfill = nullptr;
+    h->dnear = nullptr;
     h->nfill = 0;
   }
   if (nsolid == 0) return LBM_OK;  // no obstacles: the fused kernels
@@ -764,6 +840,15 @@ int lbm_set_solid(lbm_handle* h, const uint8_t* solid) {
   } else {
     const Phys<float> P = make_phys<float>(h);
     CUDA_TRY(h, launch_obs_links<float>(P, (const unsigned char*)h->dstage, h->dobs, h->stream));
+  }
+  if (h->use_tma && h->prm.phase_model == LBM_AC && h->nx >= 4 * XPAD) {
+    switch (h->prec) {
+      case LBM_FP64: rc = build_near_map<PopPlain<double>>(h, solid); break;
+      case LBM_FP32: rc = build_near_map<PopPlain<float>>(h, solid); break;
+      case LBM_FP16_DEV: rc = build_near_map<PopDev<__half>>(h, solid); break;
+      default: rc = build_near_map<PopDev<__nv_bfloat16>>(h, solid); break;
+    }
+    if (rc) return rc;
   }
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   return LBM_OK;

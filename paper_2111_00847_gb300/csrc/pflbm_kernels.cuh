@@ -99,6 +99,11 @@ struct Phys {
   // y * nx + x): the only solid nodes a fluid stencil reads
   const int* obs_fill;
   int obs_nfill;
+  // per block of the Allen-Cahn TMA step's launch grid: nonzero when a solid
+  // node lies within 3 nodes of the block's rows and columns (nullptr: every
+  // block); blocks away from obstacles take the plain step's path
+  const uint8_t* obs_near;
+  int obs_box[4];  // x_lo, x_hi, y_lo, y_hi: where those blocks read phi from the filled plane
 };
 constexpr int OBS_SOLID = 8;
 
@@ -1137,6 +1142,8 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
   const T isf = P.dv_is[0], isg = P.dv_is[1];
   const int f_last = y1 + 1, g_last = y1;  // last f / g row any output row needs
   const bool edge_x = wx && (x0 == 0 || x0 + w == nx);  // strip touches an x wall
+  // OBS: this block reaches a solid node (else it runs the plain step's path)
+  const bool near = OBS && (!P.obs_near || P.obs_near[blockIdx.y * gridDim.x + blockIdx.x]);
 
   if (tid == 0) {
     for (int k = 0; k < RF + RG; ++k) mbar_init(&barF[k], 1);
@@ -1162,8 +1169,6 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
   };
   auto fslot = [&](int r) { return sf + ((r - fbase) % RF) * FS; };
   auto gslot = [&](int r) { return sg + ((r - gbase) % RG) * FS; };
-  auto stage_f = [&](int r) { stage(B.fin, fslot(r), &barF[(r - fbase) % RF], r); };
-  auto stage_g = [&](int r) { stage(B.gin, gslot(r), &barG[(r - gbase) % RG], r); };
   auto wait_f = [&](int r) {
     const int li = r - fbase;
     return mbar_wait_bounded(&barF[li % RF], (li / RF) & 1);
@@ -1195,7 +1200,7 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
     const int rr = wrap_row(r);
     const bool bym = wy && rr == 0, byp = wy && rr == ny - 1;
     T* dst = sp + tslot(r) * (TBX + 2);
-    if constexpr (OBS) {
+    if (OBS && near) {
       phi_row_plane(r);
       if (FK && keep && active) {
         mnext = P.obs[(long long)rr * nx + x];
@@ -1242,7 +1247,7 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
   // SLIM: phi of row y0 - 1 (in the domain or wrapped) from pulls of the
   // global planes, since its f rows are not staged.
   auto phi_row_global = [&](int r) {
-    if constexpr (OBS) {
+    if (OBS && near) {
       phi_row_plane(r);
       return;
     }
@@ -1280,8 +1285,8 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
   // that the ghost row below it can be formed before the march).
   const bool bottom = wy && y0 == 0;
   if (tid == 0) {
-    for (int r = fbase; r <= min(y0 + 1 + DF, f_last); ++r) stage_f(r);
-    for (int r = gbase; r <= min(y0 + DG, g_last); ++r) stage_g(r);
+    for (int r = fbase; r <= min(y0 + 1 + DF, f_last); ++r) stage(B.fin, fslot(r), &barF[(r - fbase) % RF], r);
+    for (int r = gbase; r <= min(y0 + DG, g_last); ++r) stage(B.gin, gslot(r), &barG[(r - gbase) % RG], r);
   }
   for (int r = fbase; r <= min(y0 + (bottom ? 2 : 1), f_last); ++r) ok = wait_f(r) && ok;
   for (int r = gbase; r <= min(y0, g_last); ++r) ok = wait_g(r) && ok;
@@ -1371,7 +1376,7 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
       const unsigned char* g_p = sg + add(gA, 2, RG) * FS;
       const bool bym = wy && y == 0, byp = wy && y == ny - 1;
       T g[9];
-      if constexpr (OBS) {
+      if (OBS && near) {
         if (!FK) mc = P.obs[(long long)y * nx + x];
         if (!FK) pull_staged_obs<C, SEG>(f_m, f_0, f_p, tid + XPAD, mc, rf2, isf, f);
         pull_staged_obs<C, SEG>(g_m, g_0, g_p, tid + XPAD, mc, rg2, isg, g);
@@ -1383,7 +1388,7 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
         if (!FK) pull_staged<C, SEG>(f_m, f_0, f_p, tid + XPAD, false, false, false, false, rf2, isf, f);
         pull_staged<C, SEG>(g_m, g_0, g_p, tid + XPAD, false, false, false, false, rg2, isg, g);
       }
-      if (OBS && ((mc >> OBS_SOLID) & 1u)) {  // a solid node: no populations, no history
+      if (OBS && near && ((mc >> OBS_SOLID) & 1u)) {  // a solid node: no populations, no history
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = T(0);
         store_pops<C>(P, B.fout, 0, x, y, f, T(0), true);

@@ -82,6 +82,13 @@ static cudaError_t launch_tma_variant(const Phys<typename C::value_t>& P0, const
                           : launch_tma_seg<C, UR, true, OBS>(P, B, err, s);
 }
 
+// Launch grid of the Allen-Cahn TMA step (strip width, rows per segment).
+template <class C>
+void tma_step_grid(int nx, int ny, int* tbx, int* seg_rows) {
+  *tbx = TmaCfg<C>::TBX;
+  *seg_rows = tma_segment_rows<C>(nx, ny);
+}
+
 // Cahn-Hilliard step: same segment rule, its own launch shape (TmaChCfg).
 template <class C>
 static int tma_ch_segment_rows(int nx, int ny) {
@@ -184,7 +191,7 @@ static cudaError_t obs_passes(const Phys<typename C::value_t>& P, const Bufs<typ
   using T = typename C::value_t;
   const dim3 grid = row_grid(P.nx, P.ny, OBS_THREADS);
   const int fill_blocks = (P.obs_nfill + OBS_THREADS - 1) / OBS_THREADS;
-  k_obs_phi<C, MODE == MODE_INIT ? MODE_INIT : MODE_STEP><<<grid, OBS_THREADS, 0, s>>>(P, B, phis);
+  k_obs_phi<C, MODE == MODE_INIT ? MODE_INIT : MODE_STEP><<<grid, OBS_THREADS, 0, s>>>(P, B, phis, 0, P.nx, 0);
   if (fill_blocks) k_obs_fill<T><<<fill_blocks, OBS_THREADS, 0, s>>>(P, phis);
   if (MODEL == MODEL_CH) {
     k_obs_mu<T><<<grid, OBS_THREADS, 0, s>>>(P, phis, mus);
@@ -209,15 +216,20 @@ static cudaError_t obs_model(int mode, const Phys<typename C::value_t>& P, const
   }
 }
 
-// Allen-Cahn step with obstacles on the TMA kernel: phi and its fill, then
-// k_step_tma<..., OBS> reading phi from the plane.
+// Allen-Cahn step with obstacles on the TMA kernel: phi and its fill over
+// the region the blocks near obstacles read (P.obs_box; the whole grid
+// without P.obs_near), then k_step_tma<..., OBS>, whose near blocks read phi
+// from the plane and the others run the plain step's path.
 template <class C>
 static cudaError_t obs_step_tma(const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B0,
                                 typename C::value_t* phis, int* err, bool unit_rates, cudaStream_t s) {
   using T = typename C::value_t;
-  const dim3 grid = row_grid(P.nx, P.ny, OBS_THREADS);
+  const int x_lo = P.obs_near ? P.obs_box[0] : 0, x_hi = P.obs_near ? P.obs_box[1] : P.nx;
+  const int y_lo = P.obs_near ? P.obs_box[2] : 0, y_hi = P.obs_near ? P.obs_box[3] : P.ny;
   const int fill_blocks = (P.obs_nfill + OBS_THREADS - 1) / OBS_THREADS;
-  k_obs_phi<C, MODE_STEP><<<grid, OBS_THREADS, 0, s>>>(P, B0, phis);
+  if (x_hi > x_lo && y_hi > y_lo)
+    k_obs_phi<C, MODE_STEP><<<row_grid(x_hi - x_lo, y_hi - y_lo, OBS_THREADS), OBS_THREADS, 0, s>>>(P, B0, phis, x_lo,
+                                                                                                   x_hi, y_lo);
   if (fill_blocks) k_obs_fill<T><<<fill_blocks, OBS_THREADS, 0, s>>>(P, phis);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -235,7 +247,7 @@ static cudaError_t obs_step_tma_ch(const Phys<typename C::value_t>& P0, const Bu
   using T = typename C::value_t;
   const dim3 grid = row_grid(P0.nx, P0.ny, OBS_THREADS);
   const int fill_blocks = (P0.obs_nfill + OBS_THREADS - 1) / OBS_THREADS;
-  k_obs_phi<C, MODE_STEP><<<grid, OBS_THREADS, 0, s>>>(P0, B0, phis);
+  k_obs_phi<C, MODE_STEP><<<grid, OBS_THREADS, 0, s>>>(P0, B0, phis, 0, P0.nx, 0);
   if (fill_blocks) k_obs_fill<T><<<fill_blocks, OBS_THREADS, 0, s>>>(P0, phis);
   k_obs_mu<T><<<grid, OBS_THREADS, 0, s>>>(P0, phis, mus);
   if (fill_blocks) k_obs_fill<T><<<fill_blocks, OBS_THREADS, 0, s>>>(P0, mus);
@@ -319,7 +331,8 @@ cudaError_t launch_adjoint_init(const Phys<T>& P, const AdjBufs& A, double* out,
   template cudaError_t launch_step_tma_ch<C>(const Phys<C::value_t>&, const Bufs<C::value_t>&, int*, \
                                              bool, cudaStream_t);                                   \
   template cudaError_t launch_obs<C>(int, int, const Phys<C::value_t>&, const Bufs<C::value_t>&,    \
-                                     C::value_t*, C::value_t*, bool, int*, bool, cudaStream_t);
+                                     C::value_t*, C::value_t*, bool, int*, bool, cudaStream_t);     \
+  template void tma_step_grid<C>(int, int, int*, int*);
 
 #define PFLBM_INSTANTIATE_DEV(C)                                                                    \
   PFLBM_INSTANTIATE_CODEC(C)                                                                        \

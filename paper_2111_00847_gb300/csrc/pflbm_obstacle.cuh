@@ -63,13 +63,14 @@ __global__ void k_obs_links(const Phys<T> P, const unsigned char* __restrict__ s
 // phi at every fluid node (INIT: the given field).  Solid entries are left
 // alone: k_obs_fill writes the ones a fluid stencil reads.  The plane has the
 // one-plane row layout ix(P, 1, 0, x, y).
+// Over the nodes [x_lo, x_hi) x [y_lo, y_hi) of the grid (blockIdx.y: the row).
 template <class C, int MODE>
 __global__ void k_obs_phi(const Phys<typename C::value_t> P, const Bufs<typename C::value_t> B,
-                          typename C::value_t* __restrict__ phis) {
+                          typename C::value_t* __restrict__ phis, int x_lo, int x_hi, int y_lo) {
   using T = typename C::value_t;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y;
-  if (x >= P.nx) return;
+  const int x = x_lo + blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = y_lo + blockIdx.y;
+  if (x >= x_hi) return;
   const unsigned m = P.obs[(long long)y * P.nx + x];
   T v;
   if (MODE == MODE_INIT) {
