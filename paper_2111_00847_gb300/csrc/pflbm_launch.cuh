@@ -192,7 +192,6 @@ static cudaError_t obs_passes(const Phys<typename C::value_t>& P, const Bufs<typ
   const dim3 grid = row_grid(P.nx, P.ny, OBS_THREADS);
   const int fill_blocks = (P.obs_nfill + OBS_THREADS - 1) / OBS_THREADS;
   k_obs_phi<C, MODE == MODE_INIT ? MODE_INIT : MODE_STEP><<<grid, OBS_THREADS, 0, s>>>(P, B, phis, 0, P.nx, 0);
-  if (fill_blocks) k_obs_fill<T><<<fill_blocks, OBS_THREADS, 0, s>>>(P, phis);
   if (MODEL == MODEL_CH) {
     k_obs_mu<T><<<grid, OBS_THREADS, 0, s>>>(P, phis, mus);
     if (fill_blocks) k_obs_fill<T><<<fill_blocks, OBS_THREADS, 0, s>>>(P, mus);
@@ -226,11 +225,9 @@ static cudaError_t obs_step_tma(const Phys<typename C::value_t>& P, const Bufs<t
   using T = typename C::value_t;
   const int x_lo = P.obs_near ? P.obs_box[0] : 0, x_hi = P.obs_near ? P.obs_box[1] : P.nx;
   const int y_lo = P.obs_near ? P.obs_box[2] : 0, y_hi = P.obs_near ? P.obs_box[3] : P.ny;
-  const int fill_blocks = (P.obs_nfill + OBS_THREADS - 1) / OBS_THREADS;
   if (x_hi > x_lo && y_hi > y_lo)
     k_obs_phi<C, MODE_STEP><<<row_grid(x_hi - x_lo, y_hi - y_lo, OBS_THREADS), OBS_THREADS, 0, s>>>(P, B0, phis, x_lo,
                                                                                                    x_hi, y_lo);
-  if (fill_blocks) k_obs_fill<T><<<fill_blocks, OBS_THREADS, 0, s>>>(P, phis);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   Bufs<T> B = B0;
@@ -248,7 +245,6 @@ static cudaError_t obs_step_tma_ch(const Phys<typename C::value_t>& P0, const Bu
   const dim3 grid = row_grid(P0.nx, P0.ny, OBS_THREADS);
   const int fill_blocks = (P0.obs_nfill + OBS_THREADS - 1) / OBS_THREADS;
   k_obs_phi<C, MODE_STEP><<<grid, OBS_THREADS, 0, s>>>(P0, B0, phis, 0, P0.nx, 0);
-  if (fill_blocks) k_obs_fill<T><<<fill_blocks, OBS_THREADS, 0, s>>>(P0, phis);
   k_obs_mu<T><<<grid, OBS_THREADS, 0, s>>>(P0, phis, mus);
   if (fill_blocks) k_obs_fill<T><<<fill_blocks, OBS_THREADS, 0, s>>>(P0, mus);
   cudaError_t e = cudaGetLastError();

@@ -60,9 +60,25 @@ __global__ void k_obs_links(const Phys<T> P, const unsigned char* __restrict__ s
   obs[(long long)y * P.nx + x] = (uint16_t)m;
 }
 
-// phi at every fluid node (INIT: the given field).  Solid entries are left
-// alone: k_obs_fill writes the ones a fluid stencil reads.  The plane has the
-// one-plane row layout ix(P, 1, 0, x, y).
+// phi at every fluid node of [x_lo, x_hi) x [y_lo, y_hi) (INIT: the given
+// field), and at every solid node there with a fluid neighbour the
+// neutral-wetting value of reading 17: the mean over its fluid axis
+// neighbours, or, with none, over its fluid diagonal neighbours.  A solid
+// node forms its neighbours' phi again from their own pulls (the same sum9,
+// so the same bits as the neighbours store), so phi and its fill take one
+// pass.  Neighbour x + c_k is fluid when link opp(k) of the node does not
+// reflect.  The plane has the one-plane row layout ix(P, 1, 0, x, y).
+template <class C, int MODE>
+__device__ __forceinline__ typename C::value_t obs_phi_node(const Phys<typename C::value_t>& P,
+                                                            const Bufs<typename C::value_t>& B, int x, int y,
+                                                            unsigned m) {
+  using T = typename C::value_t;
+  if (MODE == MODE_INIT) return T(B.iphi[(long long)y * P.nx + x]);
+  T f[9];
+  pull9_obs<C>(B.fin, P, 0, x, y, m, f);
+  return sum9(f);
+}
+
 // Over the nodes [x_lo, x_hi) x [y_lo, y_hi) of the grid (blockIdx.y: the row).
 template <class C, int MODE>
 __global__ void k_obs_phi(const Phys<typename C::value_t> P, const Bufs<typename C::value_t> B,
@@ -72,15 +88,32 @@ __global__ void k_obs_phi(const Phys<typename C::value_t> P, const Bufs<typename
   const int y = y_lo + blockIdx.y;
   if (x >= x_hi) return;
   const unsigned m = P.obs[(long long)y * P.nx + x];
-  T v;
-  if (MODE == MODE_INIT) {
-    v = T(B.iphi[(long long)y * P.nx + x]);
-  } else {
-    T f[9];
-    pull9_obs<C>(B.fin, P, 0, x, y, m, f);
-    v = sum9(f);
+  if (!((m >> OBS_SOLID) & 1u)) {
+    phis[ix(P, 1, 0, x, y)] = obs_phi_node<C, MODE>(P, B, x, y, m);
+    return;
   }
-  if (!((m >> OBS_SOLID) & 1u)) phis[ix(P, 1, 0, x, y)] = v;
+  if ((m & 0xffu) == 0xffu) return;  // no fluid neighbour: no fluid stencil reads this node
+  const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  const int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  const int op[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+  T val = T(0);
+  for (int k0 = 1; k0 <= 5; k0 += 4) {
+    T sm = T(0);
+    int c = 0;
+    for (int k = k0; k < k0 + 4; ++k) {
+      if ((m >> (op[k] - 1)) & 1u) continue;
+      int xn = x + cx[k], yn = y + cy[k];
+      xn = xn < 0 ? xn + P.nx : (xn >= P.nx ? xn - P.nx : xn);
+      yn = yn < 0 ? yn + P.ny : (yn >= P.ny ? yn - P.ny : yn);
+      sm += obs_phi_node<C, MODE>(P, B, xn, yn, P.obs[(long long)yn * P.nx + xn]);
+      ++c;
+    }
+    if (c > 0) {
+      val = sm / T(c);
+      break;
+    }
+  }
+  phis[ix(P, 1, 0, x, y)] = val;
 }
 
 // Neutral-wetting value at each solid node next to fluid (P.obs_fill), from

@@ -208,11 +208,12 @@ def test_lowp_dam_break_full_size(pk, prec, capsys):
 def test_lowp_full_size_sampled_windows(pk, oracle_mod, prec):
     """The throughput workload at 16384^2 in 16-bit storage, in the launch
     configuration the benchmark times, checked on sampled windows against
-    the oracle run on the windows with a 2k margin (k = 8 steps)."""
+    the oracle run on the windows with a 2k margin (k = 100 steps, the
+    horizon of the paper-workload bars of this file)."""
     torch = pytest.importorskip("torch")
     if torch.cuda.mem_get_info()[0] < 60e9:
         pytest.skip("needs ~50 GB of device memory")
-    n, k, wy = 16384, 8, 48
+    n, k, wy = 16384, 100, 48
     m = 2 * k + 6
     case = W.rti_multimode(n, precision=prec)
     x0 = n // 3
@@ -244,5 +245,8 @@ def test_lowp_full_size_sampled_windows(pk, oracle_mod, prec):
         fo, go = ref[y0]
         ga = ga.copy()
         ga[0] -= rho0
-        assert np.abs(fa - fo).max() <= 0.2 * u * fmax, (y0, np.abs(fa - fo).max() / fmax / u)
-        assert np.abs(ga - go).max() <= 16 * u * gmax, (y0, np.abs(ga - go).max() / gmax / u)
+        ef, eg = np.abs(fa - fo).max() / fmax / u, np.abs(ga - go).max() / gmax / u
+        print(f"\n[16-bit full size, {k} steps] window y0={y0}: f {ef:.3f} u (bar 0.2 u), g {eg:.2f} u (bar 16 u)",
+              end="")
+        assert ef <= 0.2, (y0, ef)
+        assert eg <= 16, (y0, eg)
