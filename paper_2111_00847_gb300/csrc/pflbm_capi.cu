@@ -600,46 +600,39 @@ static int build_near_map(lbm_handle* h, const uint8_t* solid) {
   tma_step_grid<C>(h->nx, h->ny, &tbx, &seg);
   const int nx = h->nx, ny = h->ny;
   const bool px = h->prm.bc[LBM_LEFT] == LBM_PERIODIC, py = h->prm.bc[LBM_BOTTOM] == LBM_PERIODIC;
-  // integral image of the mask: S[(y) (nx+1) + x] = solid nodes in [0, x) x [0, y)
-  std::vector<int> S((size_t)(nx + 1) * (ny + 1), 0);
-  for (int y = 0; y < ny; ++y)
-    for (int x = 0; x < nx; ++x)
-      S[(size_t)(y + 1) * (nx + 1) + x + 1] = (solid[(size_t)y * nx + x] != 0) + S[(size_t)y * (nx + 1) + x + 1] +
-                                              S[(size_t)(y + 1) * (nx + 1) + x] - S[(size_t)y * (nx + 1) + x];
-  auto rect = [&](int xa, int xb, int ya, int yb) {
-    return S[(size_t)yb * (nx + 1) + xb] - S[(size_t)ya * (nx + 1) + xb] - S[(size_t)yb * (nx + 1) + xa] +
-           S[(size_t)ya * (nx + 1) + xa];
-  };
-  // [a, b) in a direction of n nodes -> up to two in-grid intervals
-  auto split = [](int a, int b, int n, bool periodic, int out[4]) {
-    if (!periodic) {
-      out[0] = std::max(a, 0), out[1] = std::min(b, n), out[2] = out[3] = 0;
-      return;
-    }
-    if (b - a >= n) {
-      out[0] = 0, out[1] = n, out[2] = out[3] = 0;
-      return;
-    }
-    const int a0 = ((a % n) + n) % n, e = a0 + (b - a);
-    out[0] = a0, out[1] = std::min(e, n);
-    out[2] = 0, out[3] = e > n ? e - n : 0;
-  };
   const int gx = (nx + tbx - 1) / tbx, gy = (ny + seg - 1) / seg;
   std::vector<uint8_t> nearv((size_t)gx * gy, 0);
+  // a block is near when a solid node lies in its rows and columns widened by
+  // 3; mark, for every solid node, the blocks whose widened range holds it:
+  // the blocks of the columns (rows) c - 3 .. c + 3, clamped at walls and
+  // wrapped at periodic sides (a ragged last strip or a short segment can
+  // sit wholly inside that range, so every position is looked at)
+  auto blocks_of = [](int c, int n, int width, bool periodic, int out[7]) {
+    int k = 0;
+    for (int d = -3; d <= 3; ++d) {
+      int cc = c + d;
+      if (cc < 0 || cc >= n) cc = periodic ? ((cc % n) + n) % n : std::min(std::max(cc, 0), n - 1);
+      const int b = cc / width;
+      bool seen = false;
+      for (int i = 0; i < k; ++i) seen = seen || out[i] == b;
+      if (!seen) out[k++] = b;
+    }
+    return k;
+  };
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      if (!solid[(size_t)y * nx + x]) continue;
+      int bxs[7], bys[7];
+      const int kx = blocks_of(x, nx, tbx, px, bxs), ky = blocks_of(y, ny, seg, py, bys);
+      for (int j = 0; j < ky; ++j)
+        for (int i = 0; i < kx; ++i) nearv[(size_t)bys[j] * gx + bxs[i]] = 1;
+    }
   int bx0 = nx, bx1 = 0, by0 = ny, by1 = 0;
   bool xwrap = false, ywrap = false;
   for (int by = 0; by < gy; ++by)
     for (int bx = 0; bx < gx; ++bx) {
+      if (!nearv[(size_t)by * gx + bx]) continue;
       const int x0 = bx * tbx, x1 = std::min(x0 + tbx, nx), y0 = by * seg, y1 = std::min(y0 + seg, ny);
-      int xi[4], yi[4];
-      split(x0 - 3, x1 + 3, nx, px, xi);
-      split(y0 - 3, y1 + 3, ny, py, yi);
-      long long c = 0;
-      for (int i = 0; i < 4; i += 2)
-        for (int j = 0; j < 4; j += 2)
-          if (xi[i + 1] > xi[i] && yi[j + 1] > yi[j]) c += rect(xi[i], xi[i + 1], yi[j], yi[j + 1]);
-      if (!c) continue;
-      nearv[(size_t)by * gx + bx] = 1;
       xwrap = xwrap || (px && (x0 - 2 < 0 || x1 + 2 > nx));
       ywrap = ywrap || (py && (y0 - 2 < 0 || y1 + 2 > ny));
       bx0 = std::min(bx0, std::max(x0 - 2, 0)), bx1 = std::max(bx1, std::min(x1 + 2, nx));
