@@ -1,6 +1,8 @@
 // Definitions of the launch wrappers declared in pflbm_launch.h.
 #pragma once
 
+#include <cmath>
+
 #include "pflbm_launch.h"
 
 namespace pflbm {
@@ -26,11 +28,6 @@ cudaError_t launch_march(int model, int mode, const Phys<typename C::value_t>& P
                            : launch_march_model<C, MODEL_AC>(mode, P, B, s);
 }
 
-// Rows per block segment of the TMA step: LY, halved (down to 8) until the
-// grid holds at least two waves of resident blocks, so that grids of a few
-// million nodes still fill every SM.  Each segment re-forms two phi rows and
-// re-stages its first rows, so long segments are kept wherever the grid is
-// large enough.
 // Number of SMs of the current device (looked up once per device).
 static inline int device_sm_count() {
   static int sms[64] = {0};
@@ -41,20 +38,51 @@ static inline int device_sm_count() {
   return sms[dev];
 }
 
-// Rows per block segment: LY, halved (down to 8) until a grid of strips of
-// `tbx` columns holds at least two waves of `per_sm` resident blocks.
-static inline int segment_rows(int nx, int ny, int tbx, int per_sm) {
-  const long long target = 2LL * device_sm_count() * per_sm;
+// Rows per block segment: LY, halved (down to 8) until the grid of strips of
+// `tbx` columns holds at least `waves` waves of `per_sm` resident blocks, so
+// that grids of a few million nodes still fill every SM.  Each segment
+// re-forms two phi rows and re-stages its first rows, so long segments are
+// kept wherever the grid is large enough.
+static inline int segment_rows(int nx, int ny, int tbx, int per_sm, int waves = 2) {
+  const long long target = (long long)waves * device_sm_count() * per_sm;
   const long long strips = (nx + tbx - 1) / tbx;
   int seg = LY;
   while (seg > 8 && strips * ((ny + seg - 1) / seg) < target) seg /= 2;
   return seg;
 }
 
+// Rows per segment of the FP32 Allen-Cahn step on grids that hold fewer than
+// eight waves of LY-row blocks: the length in [8, LY] with the least
+// modelled time.  A block takes time in proportion to its rows plus two (the
+// rows it re-stages first); blocks run in waves of (SMs x resident blocks),
+// and a partial last wave of this latency-bound kernel costs about half a
+// full wave beyond its share of the blocks.  Measured: 2048 x 1024 picks 23
+// rows (26.2 GLUPS, 23.9 at 8), 4096 x 2048 picks 45 (28.1, 27.4 at 32).
+static inline int segment_rows_waves(int nx, int ny, int tbx, int per_sm) {
+  const long long slots = (long long)device_sm_count() * per_sm;
+  const long long strips = (nx + tbx - 1) / tbx;
+  if (strips * ((ny + LY - 1) / LY) >= 8 * slots) return LY;
+  int pick = LY;
+  double best = 0.0;
+  for (int seg = LY; seg >= 8; --seg) {
+    const double w = (double)(strips * ((ny + seg - 1) / seg)) / (double)slots;
+    const double cost = (w + 0.5 * (std::ceil(w) - w)) * (seg + 2);
+    if (seg == LY || cost < best) best = cost, pick = seg;  // ties keep the longer segment
+  }
+  return pick;
+}
+
+// Segment rows of the Allen-Cahn TMA step.  The 16-bit deviation step is
+// bound by instruction issue, so blocks of a partial wave run faster and one
+// wave of blocks suffices; the obstacle step, whose blocks near the obstacle
+// take longer, and FP64 keep the two-wave rule.
 template <class C>
-static int tma_segment_rows(int nx, int ny) {
+static int tma_segment_rows(int nx, int ny, bool obs) {
   using G = TmaCfg<C>;
-  return segment_rows(nx, ny, G::TBX, G::threads / G::TBX);
+  const int per_sm = G::threads / G::TBX;
+  if (C::dev) return segment_rows(nx, ny, G::TBX, per_sm, 1);
+  if (G::fp32 && !obs) return segment_rows_waves(nx, ny, G::TBX, per_sm);
+  return segment_rows(nx, ny, G::TBX, per_sm);
 }
 
 template <class C, bool UR, bool VSEG, bool OBS = false>
@@ -77,16 +105,17 @@ template <class C, bool UR, bool OBS = false>
 static cudaError_t launch_tma_variant(const Phys<typename C::value_t>& P0, const Bufs<typename C::value_t>& B,
                                       int* err, cudaStream_t s) {
   Phys<typename C::value_t> P = P0;
-  P.seg_rows = tma_segment_rows<C>(P.nx, P.ny);
+  P.seg_rows = tma_segment_rows<C>(P.nx, P.ny, OBS);
   return P.seg_rows == LY ? launch_tma_seg<C, UR, false, OBS>(P, B, err, s)
                           : launch_tma_seg<C, UR, true, OBS>(P, B, err, s);
 }
 
-// Launch grid of the Allen-Cahn TMA step (strip width, rows per segment).
+// Launch grid of the Allen-Cahn TMA step with obstacles (strip width, rows
+// per segment).
 template <class C>
 void tma_step_grid(int nx, int ny, int* tbx, int* seg_rows) {
   *tbx = TmaCfg<C>::TBX;
-  *seg_rows = tma_segment_rows<C>(nx, ny);
+  *seg_rows = tma_segment_rows<C>(nx, ny, true);
 }
 
 // Cahn-Hilliard step: same segment rule, its own launch shape (TmaChCfg).
