@@ -40,6 +40,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <climits>
 #include <type_traits>
 
 namespace pflbm {
@@ -1184,16 +1185,41 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
   T fnext[9];  // FK: the pulled f of the last phi row made with keep set
   unsigned mnext = 0;  // OBS and FK: the link word of that row's node
   // OBS: phi of row r from the filled plane (x-wall ghosts as in the plain
-  // step, from the plane's columns 0, 1 and nx-1, nx-2)
-  auto phi_row_plane = [&](int r) {
-    const int rr = wrap_row(r);
-    T* dst = sp + tslot(r) * (TBX + 2);
+  // step, from the plane's columns 0, 1 and nx-1, nx-2).  The plane values
+  // and the link word (FK) of a row are loaded one march step before the
+  // row is formed, so that their latency overlaps a node update.
+  int pre_r = INT_MIN;  // the row whose values the pre_ registers hold
+  T pre_c = T(0), pre_l0 = T(0), pre_l1 = T(0), pre_r0 = T(0), pre_r1 = T(0);
+  unsigned pre_m = 0;
+  const bool wl = wx && x0 == 0, wr = wx && x0 + w == nx;  // the strip ends at an x wall
+  auto plane_load = [&](int r) {
+    pre_r = r;
     if (!active) return;
+    const int rr = wrap_row(r);
     const T* pr = B.phis + ix(P, 1, 0, 0, rr);
-    dst[tid + 1] = pr[x];
-    if (tid == 0) dst[0] = x0 > 0 ? pr[x0 - 1] : (!wx ? pr[nx - 1] : wall_ghost(P, SIDE_LEFT, pr[0], pr[1]));
-    if (tid == w - 1)
-      dst[w + 1] = x0 + w < nx ? pr[x0 + w] : (!wx ? pr[0] : wall_ghost(P, SIDE_RIGHT, pr[nx - 1], pr[nx - 2]));
+    pre_c = pr[x];
+    if (FK) pre_m = P.obs[(long long)rr * nx + x];
+    if (tid == 0) {
+      pre_l0 = x0 > 0 ? pr[x0 - 1] : (!wx ? pr[nx - 1] : pr[0]);
+      if (wl) pre_l1 = pr[1];
+    }
+    if (tid == w - 1) {
+      pre_r0 = x0 + w < nx ? pr[x0 + w] : (!wx ? pr[0] : pr[nx - 1]);
+      if (wr) pre_r1 = pr[nx - 2];
+    }
+  };
+  // returns the link word of row r's node (FK)
+  auto phi_row_plane = [&](int r) -> unsigned {
+    if (pre_r != r) plane_load(r);
+    T* dst = sp + tslot(r) * (TBX + 2);
+    const unsigned m = pre_m;
+    if (active) {
+      dst[tid + 1] = pre_c;
+      if (tid == 0) dst[0] = wl ? wall_ghost(P, SIDE_LEFT, pre_l0, pre_l1) : pre_l0;
+      if (tid == w - 1) dst[w + 1] = wr ? wall_ghost(P, SIDE_RIGHT, pre_r0, pre_r1) : pre_r0;
+    }
+    if (r + 1 <= y1 && (r + 1 < ny || !wy)) plane_load(r + 1);  // the next phi row of the march
+    return m;
   };
   auto phi_row_at = [&](int r, const unsigned char* rm, const unsigned char* r0, const unsigned char* rp,
                         bool keep) {
@@ -1201,9 +1227,9 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
     const bool bym = wy && rr == 0, byp = wy && rr == ny - 1;
     T* dst = sp + tslot(r) * (TBX + 2);
     if (OBS && near) {
-      phi_row_plane(r);
+      const unsigned m = phi_row_plane(r);
       if (FK && keep && active) {
-        mnext = P.obs[(long long)rr * nx + x];
+        mnext = m;
         pull_staged_obs<C, SEG>(rm, r0, rp, tid + XPAD, mnext, rf2, isf, fnext);
       }
       return;

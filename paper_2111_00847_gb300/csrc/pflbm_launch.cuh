@@ -72,16 +72,16 @@ static inline int segment_rows_waves(int nx, int ny, int tbx, int per_sm) {
   return pick;
 }
 
-// Segment rows of the Allen-Cahn TMA step.  The 16-bit deviation step is
-// bound by instruction issue, so blocks of a partial wave run faster and one
-// wave of blocks suffices; the obstacle step, whose blocks near the obstacle
-// take longer, and FP64 keep the two-wave rule.
+// Segment rows of the Allen-Cahn TMA step (with or without obstacles).  The
+// 16-bit deviation step is bound by instruction issue, so blocks of a
+// partial wave run faster and one wave of blocks suffices; FP64 keeps the
+// two-wave rule.
 template <class C>
-static int tma_segment_rows(int nx, int ny, bool obs) {
+static int tma_segment_rows(int nx, int ny) {
   using G = TmaCfg<C>;
   const int per_sm = G::threads / G::TBX;
   if (C::dev) return segment_rows(nx, ny, G::TBX, per_sm, 1);
-  if (G::fp32 && !obs) return segment_rows_waves(nx, ny, G::TBX, per_sm);
+  if (G::fp32) return segment_rows_waves(nx, ny, G::TBX, per_sm);
   return segment_rows(nx, ny, G::TBX, per_sm);
 }
 
@@ -105,17 +105,16 @@ template <class C, bool UR, bool OBS = false>
 static cudaError_t launch_tma_variant(const Phys<typename C::value_t>& P0, const Bufs<typename C::value_t>& B,
                                       int* err, cudaStream_t s) {
   Phys<typename C::value_t> P = P0;
-  P.seg_rows = tma_segment_rows<C>(P.nx, P.ny, OBS);
+  P.seg_rows = tma_segment_rows<C>(P.nx, P.ny);
   return P.seg_rows == LY ? launch_tma_seg<C, UR, false, OBS>(P, B, err, s)
                           : launch_tma_seg<C, UR, true, OBS>(P, B, err, s);
 }
 
-// Launch grid of the Allen-Cahn TMA step with obstacles (strip width, rows
-// per segment).
+// Launch grid of the Allen-Cahn TMA step (strip width, rows per segment).
 template <class C>
 void tma_step_grid(int nx, int ny, int* tbx, int* seg_rows) {
   *tbx = TmaCfg<C>::TBX;
-  *seg_rows = tma_segment_rows<C>(nx, ny, true);
+  *seg_rows = tma_segment_rows<C>(nx, ny);
 }
 
 // Cahn-Hilliard step: same segment rule, its own launch shape (TmaChCfg).

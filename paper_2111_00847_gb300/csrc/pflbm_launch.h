@@ -22,7 +22,7 @@ cudaError_t launch_march(int model, int mode, const Phys<typename C::value_t>& P
 template <class C>
 cudaError_t launch_step_tma(const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B, int* err,
                             bool unit_rates, cudaStream_t s);
-// its launch grid with obstacles: strip width and rows per segment on the current device
+// its launch grid: strip width and rows per segment on the current device
 template <class C>
 void tma_step_grid(int nx, int ny, int* tbx, int* seg_rows);
 // TMA-staged Cahn-Hilliard step (the same contract)
