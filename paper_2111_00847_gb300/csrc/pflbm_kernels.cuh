@@ -1599,6 +1599,12 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
       }
     }
   };
+  // the threads that form the halo columns' phi from staged rows: lane 0 of
+  // warps 1 and 2 on strips wider than two warps (thread 0, in warp 0,
+  // issues the row copies), threads 0 and w - 1 where a halo column is a
+  // wall ghost (it needs their own phi) or the strip is narrower
+  const int tl = (w > 64 && !(wx && x0 == 0)) ? 32 : 0;
+  const int tr = (w > 64 && !(wx && (x0 + w == nx || x0 + w + 1 == nx))) ? 64 : w - 1;
   auto phi_row_at = [&](int r, const unsigned char* rm, const unsigned char* r0, const unsigned char* rp) {
     if constexpr (OBS) {
       phi_row_plane(r);
@@ -1615,7 +1621,7 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
       pull_staged<C, SEG>(rm, r0, rp, tid + XPAD, false, false, false, false, rf2, isf, v);
     const T ph = sum9(v);
     dst[tid + 2] = ph;
-    if (tid == 0) {
+    if (tid == tl) {
       if (x0 > 0 || !wx) {
         pull_staged<C, SEG>(rm, r0, rp, XPAD - 1, false, wx && x0 - 1 == nx - 1, bym, byp, rf2, isf, v);
         dst[1] = sum9(v);
@@ -1627,7 +1633,7 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
         dst[0] = T(0);
       }
     }
-    if (tid == w - 1) {
+    if (tid == tr) {
       if (x0 + w < nx || !wx) {
         pull_staged<C, SEG>(rm, r0, rp, XPAD + w, wx && x0 + w == 0, wx && x0 + w == nx - 1, bym, byp, rf2, isf,
                             v);
