@@ -63,7 +63,11 @@ enum {
  *     f, 0 for the Cahn-Hilliard f, -9 w_i / 5 for g; s a power of two).
  *     The stored f_0 is solved so that a node's nine decoded f sum to its
  *     phi, so total phi is conserved independently of the 16-bit rounding.
- *     An extension beyond the paper, which computes in double precision. */
+ *     FP16_DEV takes s = 2^(13 - ceil(log2 m)) with m = max(|phi_A|, |phi_B|)
+ *     for f and max(rho_A, rho_B) for g, and needs both m in (2^-12, 2^28]
+ *     (else LBM_EINVAL) so that s and 1/s are exact FP16 values; BF16_DEV
+ *     takes s = 1.  An extension beyond the paper, which computes in double
+ *     precision. */
 enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16_DEV = 2, LBM_BF16_DEV = 3 };
 /* lbm_params.phase_model: D(phi) of Eq. (1) */
 enum { LBM_AC = 0 /* Eq. (7), conservative Allen-Cahn */, LBM_CH = 1 /* Eq. (6), Cahn-Hilliard */ };

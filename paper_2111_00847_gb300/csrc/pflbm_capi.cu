@@ -154,6 +154,14 @@ static int validate(const lbm_params* P) {
   }
   const double amax = 4.0 / (P->width * (P->phiA - P->phiB));
   if (8.0 / 3.0 - amax * std::fabs(P->phiA + P->phiB) <= 0.0) return fail(nullptr, LBM_EINVAL, "interface width too small for the wetting root");
+  if (P->precision == LBM_FP16_DEV) {
+    // the FP16 deviation scale 2^(13 - ceil(log2 m)) and its inverse, which the
+    // decode applies as an FP16 operand, must be powers of two FP16 holds
+    // exactly: m = max(|phi_A|, |phi_B|) and m = max(rho_A, rho_B) in (2^-12, 2^28]
+    const double pm = std::max(std::fabs(P->phiA), std::fabs(P->phiB)), rm = std::max(P->rhoA, P->rhoB);
+    if (!(pm > 0x1p-12 && pm <= 0x1p28 && rm > 0x1p-12 && rm <= 0x1p28))
+      return fail(nullptr, LBM_EINVAL, "FP16 deviation storage needs max |phi_A|, |phi_B| and max rho in (2^-12, 2^28]");
+  }
   if (P->diag_every < 0) return fail(nullptr, LBM_EINVAL, "diag_every < 0");
   if (P->flags & ~LBM_FLAG_NO_TMA) return fail(nullptr, LBM_EINVAL, "unknown flags 0x%x", P->flags);
   return LBM_OK;

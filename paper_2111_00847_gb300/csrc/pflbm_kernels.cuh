@@ -150,6 +150,19 @@ __device__ __forceinline__ float dec16(__half, uint16_t q) { return __half2float
 __device__ __forceinline__ float dec16(__nv_bfloat16, uint16_t q) {
   return __bfloat162float(__ushort_as_bfloat16(q));
 }
+// q * s + c in one mixed-precision FMA (16-bit q and s, FP32 c and result).
+// With s a power of two that Q holds exactly, q * s is exact and this equals
+// fmaf(dec16(q), float(s), c) bit for bit, without the separate conversion.
+__device__ __forceinline__ float fma16(__half, uint16_t q, uint16_t s, float c) {
+  float d;
+  asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(q), "h"(s), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float fma16(__nv_bfloat16, uint16_t q, uint16_t s, float c) {
+  float d;
+  asm("fma.rn.f32.bf16 %0, %1, %2, %3;" : "=f"(d) : "h"(q), "h"(s), "f"(c));
+  return d;
+}
 
 template <typename T>
 struct Bufs {
@@ -321,10 +334,11 @@ __device__ __forceinline__ void store_pops(const Phys<typename C::value_t>& P, v
     const float b = v[0];
     uint16_t q[9];
     float sq = 0.f;
+    const uint16_t is16 = enc16(Q(), is);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
       q[i] = enc16(Q(), (v[i] - P.dv_r[set][i >= 5] * b) * s);
-      sq += dec16(Q(), q[i]) * is;
+      sq = fma16(Q(), q[i], is16, sq);
     }
     const float b0 = conserve ? P.dv_c0 * (m0 - sq) : b;
     unsigned char* const rb = static_cast<unsigned char*>(buf_) + (long long)y * pop_row_bytes<C>(pc);
@@ -1028,7 +1042,7 @@ __device__ __forceinline__ typename C::value_t stg_ld(const unsigned char* slot,
     const float b = reinterpret_cast<const float*>(slot)[c];
     if (i == 0) return b;
     const uint16_t q = reinterpret_cast<const uint16_t*>(slot + SEG * C::B0)[(i - 1) * SEG + c];
-    return fmaf(dec16(typename C::raw_t(), q), is, r2[i >= 5] * b);
+    return fma16(typename C::raw_t(), q, enc16(typename C::raw_t(), is), r2[i >= 5] * b);
   }
 }
 

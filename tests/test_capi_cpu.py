@@ -68,6 +68,7 @@ def _bad(prm_kw):
     (dict(precision=7), -1), (dict(flux_model=W.FLUX_CORRECTED), -5),
     (dict(phase_model=7), -1), (dict(nx=70000, ny=70000), -1), (dict(flags=8), -1),
     (dict(n_delta=-1e-3), -1),
+    (dict(precision=W.PREC_FP16_DEV, rhoA=3e8), -1), (dict(precision=W.PREC_FP16_DEV, phiA=1e-4, phiB=0.0), -1),
 ])
 def test_create_rejects_bad_parameters(pk, kw, code):
     with pytest.raises(pk.LbmError) as ei:
