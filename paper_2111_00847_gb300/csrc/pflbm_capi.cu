@@ -64,8 +64,9 @@ struct lbm_handle {
   void* obs_planes = nullptr;
   int* dfill = nullptr;  // solid nodes next to fluid (dense indices)
   int nfill = 0;
-  uint8_t* dnear = nullptr;  // per block of the Allen-Cahn TMA step: reaches a solid node
-  int near_box[4] = {0, 0, 0, 0};  // phi-plane region those blocks read (x_lo, x_hi, y_lo, y_hi)
+  uint8_t* dnear = nullptr;  // per block of the TMA step's launch grid: reaches a solid node
+  int near_box[4] = {0, 0, 0, 0};     // phi-plane region the passes fill for them (x_lo, x_hi, y_lo, y_hi)
+  int near_box_mu[4] = {0, 0, 0, 0};  // the same for the mu_phi plane (Cahn-Hilliard)
   // y-slab of a larger grid (lbm_create_slab): rows [slab_y0, slab_y0 +
   // slab_own) of the global grid, held as local rows [ghost_lo, ghost_lo +
   // slab_own) between ghost rows that the halo exchange fills
@@ -265,7 +266,7 @@ static Phys<T> make_phys(const lbm_handle* h) {
   P.obs_fill = h->dfill;
   P.obs_nfill = h->nfill;
   P.obs_near = h->dnear;
-  for (int k = 0; k < 4; ++k) P.obs_box[k] = h->near_box[k];
+  for (int k = 0; k < 4; ++k) P.obs_box[k] = h->near_box[k], P.obs_box_mu[k] = h->near_box_mu[k];
   P.diag_y0 = h->slab ? h->ghost_lo : 0;
   P.diag_y1 = h->slab ? h->ghost_lo + h->slab_own : h->ny;
   return P;
@@ -594,18 +595,22 @@ static int do_set_fields(lbm_handle* h, int which, const double* in) {
     default: return fn<PopDev<__nv_bfloat16>>(__VA_ARGS__);                \
   }
 
-// Solid obstacles on the Allen-Cahn TMA step: which blocks of its launch
-// grid reach a solid node (within 3 nodes of their rows and columns: the
-// pulls, the phi stencil and the fill of a solid neighbour reach 3), and the
-// region of the phi plane those blocks read (their rows and columns widened
-// by 2, the reach of their phi ring and of the fill).  Blocks away from
-// obstacles run the plain step's path, so the per-step phi pass covers only
-// that region.  Periodic sides wrap; a region that wraps takes the whole
-// extent of its direction.
+// Solid obstacles on the TMA steps: which blocks of the step's launch grid
+// reach a solid node (within 3 nodes of their rows and columns: the pulls
+// and the phi ring, whose nodes pull from one node further, reach 3), and
+// the regions of the planes the per-step passes fill for those blocks.  The
+// Allen-Cahn blocks read phi up to 1 node beyond their rows and columns and
+// the phi pass forms its fill itself, so phi covers them widened by 2.  The
+// Cahn-Hilliard blocks read phi up to 2 nodes beyond and mu_phi up to 1;
+// the mu_phi fill reads mu_phi one node further and mu_phi reads phi one node
+// further, so mu_phi covers them widened by 2 and phi widened by 3.  Blocks
+// away from obstacles run the plain step's path.  Periodic sides wrap; a
+// region that wraps takes the whole extent of its direction.
 template <class C>
-static int build_near_map(lbm_handle* h, const uint8_t* solid) {
+static int build_near_map(lbm_handle* h, const uint8_t* solid, bool ch) {
   int tbx = 0, seg = 0;
-  tma_step_grid<C>(h->nx, h->ny, &tbx, &seg);
+  if (ch) tma_ch_step_grid<C>(h->nx, h->ny, &tbx, &seg);
+  else tma_step_grid<C>(h->nx, h->ny, &tbx, &seg);
   const int nx = h->nx, ny = h->ny;
   const bool px = h->prm.bc[LBM_LEFT] == LBM_PERIODIC, py = h->prm.bc[LBM_BOTTOM] == LBM_PERIODIC;
   const int gx = (nx + tbx - 1) / tbx, gy = (ny + seg - 1) / seg;
@@ -635,21 +640,26 @@ static int build_near_map(lbm_handle* h, const uint8_t* solid) {
       for (int j = 0; j < ky; ++j)
         for (int i = 0; i < kx; ++i) nearv[(size_t)bys[j] * gx + bxs[i]] = 1;
     }
-  int bx0 = nx, bx1 = 0, by0 = ny, by1 = 0;
-  bool xwrap = false, ywrap = false;
-  for (int by = 0; by < gy; ++by)
-    for (int bx = 0; bx < gx; ++bx) {
-      if (!nearv[(size_t)by * gx + bx]) continue;
-      const int x0 = bx * tbx, x1 = std::min(x0 + tbx, nx), y0 = by * seg, y1 = std::min(y0 + seg, ny);
-      xwrap = xwrap || (px && (x0 - 2 < 0 || x1 + 2 > nx));
-      ywrap = ywrap || (py && (y0 - 2 < 0 || y1 + 2 > ny));
-      bx0 = std::min(bx0, std::max(x0 - 2, 0)), bx1 = std::max(bx1, std::min(x1 + 2, nx));
-      by0 = std::min(by0, std::max(y0 - 2, 0)), by1 = std::max(by1, std::min(y1 + 2, ny));
-    }
-  h->near_box[0] = xwrap ? 0 : bx0;
-  h->near_box[1] = xwrap ? nx : bx1;
-  h->near_box[2] = ywrap ? 0 : by0;
-  h->near_box[3] = ywrap ? ny : by1;
+  // the union of the near blocks' regions widened by `wd`
+  auto box_of = [&](int wd, int box[4]) {
+    int bx0 = nx, bx1 = 0, by0 = ny, by1 = 0;
+    bool xwrap = false, ywrap = false;
+    for (int by = 0; by < gy; ++by)
+      for (int bx = 0; bx < gx; ++bx) {
+        if (!nearv[(size_t)by * gx + bx]) continue;
+        const int x0 = bx * tbx, x1 = std::min(x0 + tbx, nx), y0 = by * seg, y1 = std::min(y0 + seg, ny);
+        xwrap = xwrap || (px && (x0 - wd < 0 || x1 + wd > nx));
+        ywrap = ywrap || (py && (y0 - wd < 0 || y1 + wd > ny));
+        bx0 = std::min(bx0, std::max(x0 - wd, 0)), bx1 = std::max(bx1, std::min(x1 + wd, nx));
+        by0 = std::min(by0, std::max(y0 - wd, 0)), by1 = std::max(by1, std::min(y1 + wd, ny));
+      }
+    box[0] = xwrap ? 0 : bx0;
+    box[1] = xwrap ? nx : bx1;
+    box[2] = ywrap ? 0 : by0;
+    box[3] = ywrap ? ny : by1;
+  };
+  box_of(ch ? 3 : 2, h->near_box);
+  box_of(2, h->near_box_mu);
   h->dnear = (uint8_t*)dev_alloc(h, nearv.size());
   if (!h->dnear) return fail(h, LBM_ENOMEM, "obstacle block map");
   CUDA_TRY(h, cudaMemcpyAsync(h->dnear, nearv.data(), nearv.size(), cudaMemcpyHostToDevice, h->stream));
@@ -842,12 +852,13 @@ int lbm_set_solid(lbm_handle* h, const uint8_t* solid) {
     const Phys<float> P = make_phys<float>(h);
     CUDA_TRY(h, launch_obs_links<float>(P, (const unsigned char*)h->dstage, h->dobs, h->stream));
   }
-  if (h->use_tma && h->prm.phase_model == LBM_AC && h->nx >= 4 * XPAD) {
+  if (h->use_tma && h->nx >= 4 * XPAD) {
+    const bool ch = h->prm.phase_model == LBM_CH;
     switch (h->prec) {
-      case LBM_FP64: rc = build_near_map<PopPlain<double>>(h, solid); break;
-      case LBM_FP32: rc = build_near_map<PopPlain<float>>(h, solid); break;
-      case LBM_FP16_DEV: rc = build_near_map<PopDev<__half>>(h, solid); break;
-      default: rc = build_near_map<PopDev<__nv_bfloat16>>(h, solid); break;
+      case LBM_FP64: rc = build_near_map<PopPlain<double>>(h, solid, ch); break;
+      case LBM_FP32: rc = build_near_map<PopPlain<float>>(h, solid, ch); break;
+      case LBM_FP16_DEV: rc = build_near_map<PopDev<__half>>(h, solid, ch); break;
+      default: rc = build_near_map<PopDev<__nv_bfloat16>>(h, solid, ch); break;
     }
     if (rc) return rc;
   }

@@ -100,11 +100,13 @@ struct Phys {
   // y * nx + x): the only solid nodes a fluid stencil reads
   const int* obs_fill;
   int obs_nfill;
-  // per block of the Allen-Cahn TMA step's launch grid: nonzero when a solid
-  // node lies within 3 nodes of the block's rows and columns (nullptr: every
-  // block); blocks away from obstacles take the plain step's path
+  // per block of the TMA step's launch grid (Allen-Cahn or Cahn-Hilliard):
+  // nonzero when a solid node lies within 3 nodes of the block's rows and
+  // columns (nullptr: every block); blocks away from obstacles take the
+  // plain step's path
   const uint8_t* obs_near;
-  int obs_box[4];  // x_lo, x_hi, y_lo, y_hi: where those blocks read phi from the filled plane
+  int obs_box[4];     // x_lo, x_hi, y_lo, y_hi: the region of the phi plane the passes fill for them
+  int obs_box_mu[4];  // the same for the mu_phi plane (Cahn-Hilliard)
 };
 constexpr int OBS_SOLID = 8;
 
@@ -1528,10 +1530,12 @@ struct TmaChLayout {
   static_assert(P0 % 16 == 0 && PI % 16 == 0, "bulk-copy segments must be 16-byte multiples");
 };
 
-// OBS: solid obstacles (P.obs).  The phi and mu_phi rows come from the
-// filled planes B.phis and B.mus (k_obs_phi, k_obs_mu and k_obs_fill run
-// before the launch), with the same wall ghosts and mirrors; the pulls
-// reflect the links flagged in each node's link word; solid nodes store zeros.
+// OBS: solid obstacles (P.obs).  In blocks near an obstacle (P.obs_near)
+// the phi and mu_phi rows come from the filled planes B.phis and B.mus
+// (k_obs_phi, k_obs_mu and k_obs_fill run before the launch over the regions
+// those blocks read), with the same wall ghosts and mirrors; the pulls
+// reflect the links flagged in each node's link word; solid nodes store
+// zeros.  The other blocks run the plain step's path.
 template <class C, bool UR, bool VSEG = false, bool OBS = false>
 __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaChCfg<C>::TBX)
     k_step_tma_ch(const Phys<typename C::value_t> P, const Bufs<typename C::value_t> B, int* __restrict__ err) {
@@ -1565,6 +1569,8 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
   const T isf = P.dv_is[0], isg = P.dv_is[1];
   const int f_last = y1 + 2, g_last = y1;  // last f / g row any output row needs
   const bool edge_x = wx && (x0 == 0 || x0 + w == nx);
+  // OBS: this block reaches a solid node (else it runs the plain step's path)
+  const bool near = OBS && (!P.obs_near || P.obs_near[blockIdx.y * gridDim.x + blockIdx.x]);
 
   if (tid == 0) {
     for (int k = 0; k < RF + RG; ++k) mbar_init(&barF[k], 1);
@@ -1651,7 +1657,7 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
   const int tl = (w > 64 && !(wx && x0 == 0)) ? 32 : 0;
   const int tr = (w > 64 && !(wx && (x0 + w == nx || x0 + w + 1 == nx))) ? 64 : w - 1;
   auto phi_row_at = [&](int r, const unsigned char* rm, const unsigned char* r0, const unsigned char* rp) {
-    if constexpr (OBS) {
+    if (OBS && near) {
       phi_row_plane(r);
       return;
     }
@@ -1699,7 +1705,7 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
   };
   // the same from pulls of the global planes (segment starts)
   auto phi_row_global = [&](int r) {
-    if constexpr (OBS) {
+    if (OBS && near) {
       phi_row_plane(r);
       return;
     }
@@ -1754,7 +1760,7 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
     const T* pp = prow(r + 1);
     T* d = mrow(r);
     if (!active) return;
-    if constexpr (OBS) {  // from the filled plane, mirrored at x walls
+    if (OBS && near) {  // from the filled plane, mirrored at x walls
       const T* mr = B.mus + ix(P, 1, 0, 0, wrap_row(r));
       const T mo = mr[x];
       d[lane + 1] = mo;
@@ -1874,7 +1880,7 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
       const bool bym = wy && y == 0, byp = wy && y == ny - 1;
       T f[9], g[9];
       unsigned mc = 0;
-      if constexpr (OBS) {
+      if (OBS && near) {
         mc = P.obs[(long long)y * nx + x];
         pull_staged_obs<C, SEG>(fslot(y - 1), fslot(y), fslot(y + 1), tid + XPAD, mc, rf2, isf, f);
         pull_staged_obs<C, SEG>(gslot(y - 1), gslot(y), gslot(y + 1), tid + XPAD, mc, rg2, isg, g);
@@ -1888,7 +1894,7 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
         pull_staged<C, SEG>(gslot(y - 1), gslot(y), gslot(y + 1), tid + XPAD, false, false, false, false, rg2,
                             isg, g);
       }
-      if (OBS && ((mc >> OBS_SOLID) & 1u)) {  // a solid node: no populations, no history
+      if (OBS && near && ((mc >> OBS_SOLID) & 1u)) {  // a solid node: no populations, no history
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = T(0);
         store_pops<C>(P, B.fout, 0, x, y, f, T(0), true);

@@ -117,6 +117,15 @@ void tma_step_grid(int nx, int ny, int* tbx, int* seg_rows) {
   *seg_rows = tma_segment_rows<C>(nx, ny);
 }
 
+// Launch grid of the Cahn-Hilliard TMA step.
+template <class C>
+static int tma_ch_segment_rows(int nx, int ny);
+template <class C>
+void tma_ch_step_grid(int nx, int ny, int* tbx, int* seg_rows) {
+  *tbx = TmaChCfg<C>::TBX;
+  *seg_rows = tma_ch_segment_rows<C>(nx, ny);
+}
+
 // Cahn-Hilliard step: same segment rule, its own launch shape (TmaChCfg).
 template <class C>
 static int tma_ch_segment_rows(int nx, int ny) {
@@ -221,7 +230,7 @@ static cudaError_t obs_passes(const Phys<typename C::value_t>& P, const Bufs<typ
   const int fill_blocks = (P.obs_nfill + OBS_THREADS - 1) / OBS_THREADS;
   k_obs_phi<C, MODE == MODE_INIT ? MODE_INIT : MODE_STEP><<<grid, OBS_THREADS, 0, s>>>(P, B, phis, 0, P.nx, 0);
   if (MODEL == MODEL_CH) {
-    k_obs_mu<T><<<grid, OBS_THREADS, 0, s>>>(P, phis, mus);
+    k_obs_mu<T><<<grid, OBS_THREADS, 0, s>>>(P, phis, mus, 0, P.nx, 0);
     if (fill_blocks) k_obs_fill<T><<<fill_blocks, OBS_THREADS, 0, s>>>(P, mus);
   }
   k_obs_node<C, MODEL, MODE, UR><<<grid, OBS_THREADS, 0, s>>>(P, B, phis, mus);
@@ -263,17 +272,27 @@ static cudaError_t obs_step_tma(const Phys<typename C::value_t>& P, const Bufs<t
   return unit_rates ? launch_tma_variant<C, true, true>(P, B, err, s) : launch_tma_variant<C, false, true>(P, B, err, s);
 }
 
-// Cahn-Hilliard step with obstacles on the TMA kernel: phi, mu_phi and their
-// fills, then k_step_tma_ch<..., OBS> reading both from the planes.
+// Cahn-Hilliard step with obstacles on the TMA kernel: phi with its fill and
+// mu_phi over the regions the blocks near obstacles read (P.obs_box,
+// P.obs_box_mu; the whole grid without P.obs_near), the mu_phi fill, then
+// k_step_tma_ch<..., OBS>, whose near blocks read both planes and the
+// others run the plain step's path.
 template <class C>
 static cudaError_t obs_step_tma_ch(const Phys<typename C::value_t>& P0, const Bufs<typename C::value_t>& B0,
                                    typename C::value_t* phis, typename C::value_t* mus, int* err, bool unit_rates,
                                    cudaStream_t s) {
   using T = typename C::value_t;
-  const dim3 grid = row_grid(P0.nx, P0.ny, OBS_THREADS);
+  const bool nb = P0.obs_near != nullptr;
+  const int* bp = P0.obs_box;
+  const int* bm = P0.obs_box_mu;
+  const int px0 = nb ? bp[0] : 0, px1 = nb ? bp[1] : P0.nx, py0 = nb ? bp[2] : 0, py1 = nb ? bp[3] : P0.ny;
+  const int mx0 = nb ? bm[0] : 0, mx1 = nb ? bm[1] : P0.nx, my0 = nb ? bm[2] : 0, my1 = nb ? bm[3] : P0.ny;
   const int fill_blocks = (P0.obs_nfill + OBS_THREADS - 1) / OBS_THREADS;
-  k_obs_phi<C, MODE_STEP><<<grid, OBS_THREADS, 0, s>>>(P0, B0, phis, 0, P0.nx, 0);
-  k_obs_mu<T><<<grid, OBS_THREADS, 0, s>>>(P0, phis, mus);
+  if (px1 > px0 && py1 > py0)
+    k_obs_phi<C, MODE_STEP><<<row_grid(px1 - px0, py1 - py0, OBS_THREADS), OBS_THREADS, 0, s>>>(P0, B0, phis, px0,
+                                                                                               px1, py0);
+  if (mx1 > mx0 && my1 > my0)
+    k_obs_mu<T><<<row_grid(mx1 - mx0, my1 - my0, OBS_THREADS), OBS_THREADS, 0, s>>>(P0, phis, mus, mx0, mx1, my0);
   if (fill_blocks) k_obs_fill<T><<<fill_blocks, OBS_THREADS, 0, s>>>(P0, mus);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -356,7 +375,8 @@ cudaError_t launch_adjoint_init(const Phys<T>& P, const AdjBufs& A, double* out,
                                              bool, cudaStream_t);                                   \
   template cudaError_t launch_obs<C>(int, int, const Phys<C::value_t>&, const Bufs<C::value_t>&,    \
                                      C::value_t*, C::value_t*, bool, int*, bool, cudaStream_t);     \
-  template void tma_step_grid<C>(int, int, int*, int*);
+  template void tma_step_grid<C>(int, int, int*, int*);                                               \
+  template void tma_ch_step_grid<C>(int, int, int*, int*);
 
 #define PFLBM_INSTANTIATE_DEV(C)                                                                    \
   PFLBM_INSTANTIATE_CODEC(C)                                                                        \

@@ -25,6 +25,9 @@ cudaError_t launch_step_tma(const Phys<typename C::value_t>& P, const Bufs<typen
 // its launch grid: strip width and rows per segment on the current device
 template <class C>
 void tma_step_grid(int nx, int ny, int* tbx, int* seg_rows);
+// the Cahn-Hilliard step's launch grid
+template <class C>
+void tma_ch_step_grid(int nx, int ny, int* tbx, int* seg_rows);
 // TMA-staged Cahn-Hilliard step (the same contract)
 template <class C>
 cudaError_t launch_step_tma_ch(const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B, int* err,

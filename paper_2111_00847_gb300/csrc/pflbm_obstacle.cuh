@@ -199,14 +199,15 @@ __device__ __forceinline__ void obs_gather9(const Phys<T>& P, const T* pl, int x
   for (int i = 0; i < 9; ++i) v[i] = obs_pad(P, pl, x + cx[i], y + cy[i], wet);
 }
 
-// Cahn-Hilliard: mu_phi (Eq. (5)) at fluid nodes from the filled phi plane
-// (the Laplacian of Eq. (C.10) in the fused kernels' order); 0 at solid
-// nodes until k_obs_fill.
+// Cahn-Hilliard: mu_phi (Eq. (5)) at the fluid nodes of [x_lo, x_hi) x
+// [y_lo, y_lo + gridDim.y) from the filled phi plane (the Laplacian of Eq.
+// (C.10) in the fused kernels' order); solid nodes are left to k_obs_fill.
 template <typename T>
-__global__ void k_obs_mu(const Phys<T> P, const T* __restrict__ phis, T* __restrict__ mus) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y;
-  if (x >= P.nx) return;
+__global__ void k_obs_mu(const Phys<T> P, const T* __restrict__ phis, T* __restrict__ mus, int x_lo, int x_hi,
+                         int y_lo) {
+  const int x = x_lo + blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = y_lo + blockIdx.y;
+  if (x >= x_hi) return;
   if ((P.obs[(long long)y * P.nx + x] >> OBS_SOLID) & 1u) return;  // filled by k_obs_fill
   T p[9];
   obs_gather9(P, phis, x, y, true, p);
