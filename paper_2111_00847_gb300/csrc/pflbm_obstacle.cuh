@@ -12,19 +12,22 @@
 // node is zero.
 //
 // The fill needs phi (and, for Cahn-Hilliard, mu_phi) of fluid nodes two
-// (three) nodes away, so these fields are first formed on whole planes, one
-// thread per node:
-//   k_obs_phi   phi = sum_i f_i at fluid nodes (Eq. (22a)) -> phi plane
-//   k_obs_fill  neutral-wetting values at the solid nodes next to fluid
+// (three) nodes away, so these fields are first formed on planes, one thread
+// per node:
+//   k_obs_phi   phi = sum_i f_i at fluid nodes (Eq. (22a)) and its
+//               neutral-wetting value at the solid nodes next to fluid
+//               -> phi plane
 //   k_obs_mu    (CH) mu_phi of Eq. (5) at fluid nodes -> mu plane, then
-//               k_obs_fill on it
+//   k_obs_fill  its neutral-wetting values
 // The step's node update then runs on the TMA step kernels instantiated with
-// OBS (pflbm_kernels.cuh), which read these planes.  k_obs_node is the same
-// update one thread per node: the initial state, history and macroscopic
-// passes, and the step under LBM_FLAG_NO_TMA or on grids under 16 columns.
-// It takes the stencils from the planes with the wall ghosts of Eq. (50)
-// (mirror for mu_phi), pulls with reflection at solid links, collides and
-// stores.
+// OBS (pflbm_kernels.cuh).  There only the blocks near an obstacle read the
+// planes (the others run the plain step's path), so per step the passes
+// cover only the regions those blocks read.  k_obs_node is the same update
+// one thread per node: the initial state, history and macroscopic passes,
+// and the step under LBM_FLAG_NO_TMA or on grids under 16 columns, with the
+// passes over whole planes.  It takes the stencils from the planes with the
+// wall ghosts of Eq. (50) (mirror for mu_phi), pulls with reflection at
+// solid links, collides and stores.
 #pragma once
 
 #include "pflbm_kernels.cuh"
