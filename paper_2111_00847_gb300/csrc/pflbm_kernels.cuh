@@ -1346,6 +1346,9 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
     for (int r = fbase; r <= min(y0 + 1 + DF, f_last); ++r) stage(B.fin, fslot(r), &barF[(r - fbase) % RF], r);
     for (int r = gbase; r <= min(y0 + DG, g_last); ++r) stage(B.gin, gslot(r), &barG[(r - gbase) % RG], r);
   }
+  // OBS: the phi plane comes from the pass launched before this kernel,
+  // which may still be running (this kernel is its programmatic dependent)
+  if (OBS && near) asm volatile("griddepcontrol.wait;" ::: "memory");
   for (int r = fbase; r <= min(y0 + (bottom ? 2 : 1), f_last); ++r) ok = wait_f(r) && ok;
   for (int r = gbase; r <= min(y0, g_last); ++r) ok = wait_g(r) && ok;
   for (int r = y0 - 1; r <= y0 + (bottom ? 1 : 0); ++r) {

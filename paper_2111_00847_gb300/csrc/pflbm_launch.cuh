@@ -87,7 +87,7 @@ static int tma_segment_rows(int nx, int ny) {
 
 template <class C, bool UR, bool VSEG, bool OBS = false>
 static cudaError_t launch_tma_seg(const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B,
-                                  int* err, cudaStream_t s) {
+                                  int* err, cudaStream_t s, bool dependent = false) {
   using G = TmaCfg<C>;
   using L = TmaLayout<C, G::TBX, G::DF, G::DG, G::slim>;
   // per function and device; cheap next to a step
@@ -95,6 +95,22 @@ static cudaError_t launch_tma_seg(const Phys<typename C::value_t>& P, const Bufs
                                        (int)L::bytes);
   if (e != cudaSuccess) return e;
   const dim3 grid((P.nx + G::TBX - 1) / G::TBX, (P.ny + P.seg_rows - 1) / P.seg_rows);
+  if (OBS && dependent) {
+    // a programmatic dependent of the phi pass launched just before it: the
+    // blocks away from the obstacle start while the pass finishes; the near
+    // blocks wait for it (griddepcontrol.wait) before reading its plane
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(G::TBX);
+    cfg.dynamicSmemBytes = L::bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_step_tma<C, UR, VSEG, OBS>, P, B, err);
+  }
   k_step_tma<C, UR, VSEG, OBS><<<grid, G::TBX, L::bytes, s>>>(P, B, err);
   return cudaGetLastError();
 }
@@ -103,11 +119,11 @@ static cudaError_t launch_tma_seg(const Phys<typename C::value_t>& P, const Bufs
 // register allocation is the tuned one); shorter ones the runtime-length one.
 template <class C, bool UR, bool OBS = false>
 static cudaError_t launch_tma_variant(const Phys<typename C::value_t>& P0, const Bufs<typename C::value_t>& B,
-                                      int* err, cudaStream_t s) {
+                                      int* err, cudaStream_t s, bool dependent = false) {
   Phys<typename C::value_t> P = P0;
   P.seg_rows = tma_segment_rows<C>(P.nx, P.ny);
-  return P.seg_rows == LY ? launch_tma_seg<C, UR, false, OBS>(P, B, err, s)
-                          : launch_tma_seg<C, UR, true, OBS>(P, B, err, s);
+  return P.seg_rows == LY ? launch_tma_seg<C, UR, false, OBS>(P, B, err, s, dependent)
+                          : launch_tma_seg<C, UR, true, OBS>(P, B, err, s, dependent);
 }
 
 // Launch grid of the Allen-Cahn TMA step (strip width, rows per segment).
@@ -262,14 +278,17 @@ static cudaError_t obs_step_tma(const Phys<typename C::value_t>& P, const Bufs<t
   using T = typename C::value_t;
   const int x_lo = P.obs_near ? P.obs_box[0] : 0, x_hi = P.obs_near ? P.obs_box[1] : P.nx;
   const int y_lo = P.obs_near ? P.obs_box[2] : 0, y_hi = P.obs_near ? P.obs_box[3] : P.ny;
-  if (x_hi > x_lo && y_hi > y_lo)
+  const bool pass = x_hi > x_lo && y_hi > y_lo;
+  if (pass)
     k_obs_phi<C, MODE_STEP><<<row_grid(x_hi - x_lo, y_hi - y_lo, OBS_THREADS), OBS_THREADS, 0, s>>>(P, B0, phis, x_lo,
                                                                                                    x_hi, y_lo);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   Bufs<T> B = B0;
   B.phis = phis;
-  return unit_rates ? launch_tma_variant<C, true, true>(P, B, err, s) : launch_tma_variant<C, false, true>(P, B, err, s);
+  // the step is the phi pass's programmatic dependent only right after it
+  return unit_rates ? launch_tma_variant<C, true, true>(P, B, err, s, pass)
+                    : launch_tma_variant<C, false, true>(P, B, err, s, pass);
 }
 
 // Cahn-Hilliard step with obstacles on the TMA kernel: phi with its fill and

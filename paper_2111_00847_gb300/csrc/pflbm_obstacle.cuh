@@ -87,6 +87,9 @@ template <class C, int MODE>
 __global__ void k_obs_phi(const Phys<typename C::value_t> P, const Bufs<typename C::value_t> B,
                           typename C::value_t* __restrict__ phis, int x_lo, int x_hi, int y_lo) {
   using T = typename C::value_t;
+  // a step kernel launched as this pass's programmatic dependent may start
+  // now; it waits for this grid before it reads the plane
+  asm volatile("griddepcontrol.launch_dependents;");
   const int x = x_lo + blockIdx.x * blockDim.x + threadIdx.x;
   const int y = y_lo + blockIdx.y;
   if (x >= x_hi) return;
