@@ -1792,6 +1792,10 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
     for (int r = fbase; r <= min(y0 + 2 + DF, f_last); ++r) stage(B.fin, fslot(r), &barF[fidx(r)], r);
     for (int r = gbase; r <= min(y0 + DG, g_last); ++r) stage(B.gin, gslot(r), &barG[gidx(r)], r);
   }
+  // OBS: the planes come from the passes launched before this kernel, the
+  // last of which may still be running (this kernel is its programmatic
+  // dependent)
+  if (OBS && near) asm volatile("griddepcontrol.wait;" ::: "memory");
   for (int r = fbase; r <= min(y0 + 2, f_last); ++r) ok = wait_f(r) && ok;
   for (int r = gbase; r <= min(y0, g_last); ++r) ok = wait_g(r) && ok;
   for (int r = y0 - 2; r <= y0 - 1; ++r)

@@ -85,6 +85,30 @@ static int tma_segment_rows(int nx, int ny) {
   return segment_rows(nx, ny, G::TBX, per_sm);
 }
 
+// Launch `kern` as a programmatic dependent of the kernel launched just
+// before it on `s` (it may start once every block of that kernel has issued
+// griddepcontrol.launch_dependents, and orders its reads of that kernel's
+// output with griddepcontrol.wait), or as a plain launch.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_maybe_dependent(bool dependent, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                          cudaStream_t s, Args... args) {
+  if (!dependent) {
+    kern<<<grid, block, smem, s>>>(args...);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <class C, bool UR, bool VSEG, bool OBS = false>
 static cudaError_t launch_tma_seg(const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B,
                                   int* err, cudaStream_t s, bool dependent = false) {
@@ -95,24 +119,11 @@ static cudaError_t launch_tma_seg(const Phys<typename C::value_t>& P, const Bufs
                                        (int)L::bytes);
   if (e != cudaSuccess) return e;
   const dim3 grid((P.nx + G::TBX - 1) / G::TBX, (P.ny + P.seg_rows - 1) / P.seg_rows);
-  if (OBS && dependent) {
-    // a programmatic dependent of the phi pass launched just before it: the
-    // blocks away from the obstacle start while the pass finishes; the near
-    // blocks wait for it (griddepcontrol.wait) before reading its plane
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(G::TBX);
-    cfg.dynamicSmemBytes = L::bytes;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_step_tma<C, UR, VSEG, OBS>, P, B, err);
-  }
-  k_step_tma<C, UR, VSEG, OBS><<<grid, G::TBX, L::bytes, s>>>(P, B, err);
-  return cudaGetLastError();
+  // with obstacles, a programmatic dependent of the phi pass launched just
+  // before it: the blocks away from the obstacle start while the pass
+  // finishes; the near blocks wait for it before reading its plane
+  return launch_maybe_dependent(OBS && dependent, k_step_tma<C, UR, VSEG, OBS>, grid, dim3(G::TBX), L::bytes, s, P, B,
+                                err);
 }
 
 // Segments of LY rows use the instantiation with the constant length (its
@@ -151,15 +162,15 @@ static int tma_ch_segment_rows(int nx, int ny) {
 
 template <class C, bool UR, bool VSEG, bool OBS = false>
 static cudaError_t launch_tma_ch_seg(const Phys<typename C::value_t>& P, const Bufs<typename C::value_t>& B,
-                                     int* err, cudaStream_t s) {
+                                     int* err, cudaStream_t s, bool dependent = false) {
   using G = TmaChCfg<C>;
   using L = TmaChLayout<C, G::TBX, G::DF, G::DG>;
   cudaError_t e = cudaFuncSetAttribute(k_step_tma_ch<C, UR, VSEG, OBS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (e != cudaSuccess) return e;
   const dim3 grid((P.nx + G::TBX - 1) / G::TBX, (P.ny + P.seg_rows - 1) / P.seg_rows);
-  k_step_tma_ch<C, UR, VSEG, OBS><<<grid, G::TBX, L::bytes, s>>>(P, B, err);
-  return cudaGetLastError();
+  return launch_maybe_dependent(OBS && dependent, k_step_tma_ch<C, UR, VSEG, OBS>, grid, dim3(G::TBX), L::bytes, s,
+                                P, B, err);
 }
 
 template <class C>
@@ -307,13 +318,26 @@ static cudaError_t obs_step_tma_ch(const Phys<typename C::value_t>& P0, const Bu
   const int px0 = nb ? bp[0] : 0, px1 = nb ? bp[1] : P0.nx, py0 = nb ? bp[2] : 0, py1 = nb ? bp[3] : P0.ny;
   const int mx0 = nb ? bm[0] : 0, mx1 = nb ? bm[1] : P0.nx, my0 = nb ? bm[2] : 0, my1 = nb ? bm[3] : P0.ny;
   const int fill_blocks = (P0.obs_nfill + OBS_THREADS - 1) / OBS_THREADS;
-  if (px1 > px0 && py1 > py0)
+  // phi pass (a plain launch: it reads the previous step's populations),
+  // then the mu_phi pass, the fill and the step, each a programmatic
+  // dependent of the kernel before it (each waits for that kernel's output)
+  bool prev = false;  // a pass was launched just before
+  cudaError_t e = cudaSuccess;
+  if (px1 > px0 && py1 > py0) {
     k_obs_phi<C, MODE_STEP><<<row_grid(px1 - px0, py1 - py0, OBS_THREADS), OBS_THREADS, 0, s>>>(P0, B0, phis, px0,
                                                                                                px1, py0);
-  if (mx1 > mx0 && my1 > my0)
-    k_obs_mu<T><<<row_grid(mx1 - mx0, my1 - my0, OBS_THREADS), OBS_THREADS, 0, s>>>(P0, phis, mus, mx0, mx1, my0);
-  if (fill_blocks) k_obs_fill<T><<<fill_blocks, OBS_THREADS, 0, s>>>(P0, mus);
-  cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
+    prev = true;
+  }
+  if (e == cudaSuccess && mx1 > mx0 && my1 > my0) {
+    e = launch_maybe_dependent(prev, k_obs_mu<T>, row_grid(mx1 - mx0, my1 - my0, OBS_THREADS), dim3(OBS_THREADS), 0, s,
+                               P0, (const T*)phis, mus, mx0, mx1, my0);
+    prev = true;
+  }
+  if (e == cudaSuccess && fill_blocks) {
+    e = launch_maybe_dependent(prev, k_obs_fill<T>, dim3(fill_blocks), dim3(OBS_THREADS), 0, s, P0, mus);
+    prev = true;
+  }
   if (e != cudaSuccess) return e;
   Bufs<T> B = B0;
   B.phis = phis;
@@ -321,10 +345,10 @@ static cudaError_t obs_step_tma_ch(const Phys<typename C::value_t>& P0, const Bu
   Phys<T> P = P0;
   P.seg_rows = tma_ch_segment_rows<C>(P.nx, P.ny);
   if (P.seg_rows == LY)
-    return unit_rates ? launch_tma_ch_seg<C, true, false, true>(P, B, err, s)
-                      : launch_tma_ch_seg<C, false, false, true>(P, B, err, s);
-  return unit_rates ? launch_tma_ch_seg<C, true, true, true>(P, B, err, s)
-                    : launch_tma_ch_seg<C, false, true, true>(P, B, err, s);
+    return unit_rates ? launch_tma_ch_seg<C, true, false, true>(P, B, err, s, prev)
+                      : launch_tma_ch_seg<C, false, false, true>(P, B, err, s, prev);
+  return unit_rates ? launch_tma_ch_seg<C, true, true, true>(P, B, err, s, prev)
+                    : launch_tma_ch_seg<C, false, true, true>(P, B, err, s, prev);
 }
 
 template <class C>

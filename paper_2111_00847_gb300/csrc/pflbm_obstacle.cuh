@@ -128,6 +128,11 @@ __global__ void k_obs_phi(const Phys<typename C::value_t> P, const Bufs<typename
 // does not reflect.
 template <typename T>
 __global__ void k_obs_fill(const Phys<T> P, T* __restrict__ pl) {
+  // launched as the programmatic dependent of the pass before it (and as the
+  // primary of the step after it): let the next kernel start, wait for the
+  // previous one's plane
+  asm volatile("griddepcontrol.launch_dependents;");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= P.obs_nfill) return;
   const int n = P.obs_fill[t];
@@ -211,6 +216,9 @@ __device__ __forceinline__ void obs_gather9(const Phys<T>& P, const T* pl, int x
 template <typename T>
 __global__ void k_obs_mu(const Phys<T> P, const T* __restrict__ phis, T* __restrict__ mus, int x_lo, int x_hi,
                          int y_lo) {
+  // as k_obs_fill: let the next kernel start, wait for the phi plane
+  asm volatile("griddepcontrol.launch_dependents;");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int x = x_lo + blockIdx.x * blockDim.x + threadIdx.x;
   const int y = y_lo + blockIdx.y;
   if (x >= x_hi) return;
