@@ -1170,6 +1170,14 @@ __global__ void __launch_bounds__(TmaCfg<C>::TBX, TmaCfg<C>::threads / TmaCfg<C>
     fence_mbar_init();
   }
   __syncthreads();
+  // Launched as a programmatic dependent of the kernel before it on the
+  // stream: the next kernel may be scheduled once every block of this one
+  // has started, and (without obstacles) every block waits for the kernel
+  // before it to finish before any global access.  With obstacles that
+  // kernel is the phi pass, which the blocks far from the obstacle do not
+  // read; the near blocks wait below.
+  asm volatile("griddepcontrol.launch_dependents;");
+  if (!OBS) asm volatile("griddepcontrol.wait;" ::: "memory");
 
   auto wrap_row = [&](int r) { return r < 0 ? r + ny : (r >= ny ? r - ny : r); };
   // producer side (thread 0 only)
@@ -1583,6 +1591,14 @@ __global__ void __launch_bounds__(TmaChCfg<C>::TBX, TmaChCfg<C>::threads / TmaCh
     fence_mbar_init();
   }
   __syncthreads();
+  // Launched as a programmatic dependent of the kernel before it on the
+  // stream: the next kernel may be scheduled once every block of this one
+  // has started, and (without obstacles) every block waits for the kernel
+  // before it to finish before any global access.  With obstacles that
+  // kernel is the phi pass, which the blocks far from the obstacle do not
+  // read; the near blocks wait below.
+  asm volatile("griddepcontrol.launch_dependents;");
+  if (!OBS) asm volatile("griddepcontrol.wait;" ::: "memory");
 
   auto wrap_row = [&](int r) { return r < 0 ? r + ny : (r >= ny ? r - ny : r); };
   auto stage = [&](const void* src, unsigned char* slot, uint64_t* bar, int r) {

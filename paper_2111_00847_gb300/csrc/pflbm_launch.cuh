@@ -119,11 +119,13 @@ static cudaError_t launch_tma_seg(const Phys<typename C::value_t>& P, const Bufs
                                        (int)L::bytes);
   if (e != cudaSuccess) return e;
   const dim3 grid((P.nx + G::TBX - 1) / G::TBX, (P.ny + P.seg_rows - 1) / P.seg_rows);
-  // with obstacles, a programmatic dependent of the phi pass launched just
-  // before it: the blocks away from the obstacle start while the pass
-  // finishes; the near blocks wait for it before reading its plane
-  return launch_maybe_dependent(OBS && dependent, k_step_tma<C, UR, VSEG, OBS>, grid, dim3(G::TBX), L::bytes, s, P, B,
-                                err);
+  // a programmatic dependent of the kernel before it: without obstacles the
+  // previous step (its blocks start during that step's last blocks and wait
+  // for it to finish), with obstacles the phi pass (the blocks away from the
+  // obstacle start while the pass finishes; the near blocks wait for it
+  // before reading its plane)
+  return launch_maybe_dependent(!OBS || dependent, k_step_tma<C, UR, VSEG, OBS>, grid, dim3(G::TBX), L::bytes, s, P,
+                                B, err);
 }
 
 // Segments of LY rows use the instantiation with the constant length (its
@@ -169,7 +171,7 @@ static cudaError_t launch_tma_ch_seg(const Phys<typename C::value_t>& P, const B
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (e != cudaSuccess) return e;
   const dim3 grid((P.nx + G::TBX - 1) / G::TBX, (P.ny + P.seg_rows - 1) / P.seg_rows);
-  return launch_maybe_dependent(OBS && dependent, k_step_tma_ch<C, UR, VSEG, OBS>, grid, dim3(G::TBX), L::bytes, s,
+  return launch_maybe_dependent(!OBS || dependent, k_step_tma_ch<C, UR, VSEG, OBS>, grid, dim3(G::TBX), L::bytes, s,
                                 P, B, err);
 }
 
